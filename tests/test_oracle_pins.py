@@ -1,0 +1,542 @@
+"""Pins of the oracle to facts outside itself (CPU only).
+
+Each test ties one part of the oracle to something it does not compute
+itself: published test vectors, exhaustive enumeration, closed forms from the
+paper (Eq. probsplit, bijection probability, Eq. gr, the invariance theorem),
+the paper's printed bits/key, or plain definitions (bijectivity, minimality).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1910_06416_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+WEYL = 0x9E3779B97F4A7C15
+M64 = (1 << 64) - 1
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- mixer
+def test_mixer_matches_published_splitmix64_vectors(orc):
+    for seed, k, want in _golden_rows("splitmix64_vectors.txt"):
+        state = (int(seed) + (int(k) + 1) * WEYL) & M64
+        assert orc.mix64(state) == int(want)
+
+
+def _unmix(z):
+    """Inverse of the splitmix64 finalizer, from its algebra: undo each
+    xorshift by iterating it, undo each odd multiplication by its inverse."""
+    def unxorshift(y, s):
+        x = y
+        for _ in range(64 // s + 1):
+            x = y ^ (x >> s)
+        return x & M64
+    z = unxorshift(z, 31)
+    z = (z * pow(0x94D049BB133111EB, -1, 1 << 64)) & M64
+    z = unxorshift(z, 27)
+    z = (z * pow(0xBF58476D1CE4E5B9, -1, 1 << 64)) & M64
+    return unxorshift(z, 30)
+
+
+def test_mixer_is_a_bijection(orc):
+    rng = np.random.default_rng(1)
+    for x in [0, 1, M64, 1 << 63] + [int(v) for v in rng.integers(0, 1 << 63, 200, dtype=np.int64)]:
+        assert _unmix(orc.mix64(x)) == x
+
+
+def test_input_generator_is_splitmix64():
+    got = inputs.splitmix64(1234567, 5)
+    want = [int(r[2]) for r in _golden_rows("splitmix64_vectors.txt") if r[0] == "1234567"]
+    assert [int(v) for v in got] == want
+
+
+# ---------------------------------------------------------------- fingerprints
+def test_u64_fingerprints_injective(orc):
+    keys = inputs.u64_keys(200000, 11)
+    hi, lo = orc.fingerprint_u64(keys)
+    assert np.unique(lo).shape[0] == keys.shape[0]
+    assert np.unique(hi).shape[0] == keys.shape[0]
+    # each half is a bijection of the key: invert it
+    for i in range(0, 200000, 20011):
+        assert _unmix(int(lo[i])) ^ 0xBB67AE8584CAA73B == int(keys[i])
+        assert _unmix(int(hi[i])) ^ 0x6A09E667F3BCC909 == int(keys[i])
+
+
+def test_byte_fingerprints_separate_padding_and_length(orc):
+    strings = [b"", b"a", b"a\x00", b"ab", b"ab\x00\x00\x00\x00\x00\x00", b"abcdefgh", b"abcdefgh\x00",
+               b"\x00" * 8, b"\x00" * 16, bytes(range(32)), bytes(range(31))]
+    data = np.frombuffer(b"".join(strings), dtype=np.uint8)
+    offs = np.zeros(len(strings) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(s) for s in strings])
+    hi, lo = orc.fingerprint_bytes(data, offs)
+    sig = set(zip(hi.tolist(), lo.tolist()))
+    assert len(sig) == len(strings)
+    assert len(set(lo.tolist())) == len(strings)
+    # a single 8-byte word: both chains are one mixer step then the length step
+    w = int.from_bytes(b"abcdefgh", "little")
+    a = orc.mix64(0x6A09E667F3BCC909 ^ w)
+    assert int(hi[5]) == orc.mix64((a + 8) & M64)
+    wswap = ((w >> 32) | (w << 32)) & M64
+    c = orc.mix64(0xBB67AE8584CAA73B ^ wswap)
+    assert int(lo[5]) == orc.mix64((c + 8) & M64)
+
+
+def test_byte_fingerprints_of_generated_keys_distinct(orc):
+    bk = inputs.byte_keys(300000, 1)
+    assert bk.lengths().min() >= 8 and bk.lengths().max() <= 32
+    hi, lo = orc.fingerprint_bytes(bk.data, bk.offsets)
+    assert np.unique(lo).shape[0] == bk.n
+
+
+# ---------------------------------------------------------------- buckets
+def test_bucket_is_fixed_point_inversion(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(500):
+        hi = int(rng.integers(0, 1 << 63)) * 2 + int(rng.integers(0, 2))
+        nb = int(rng.integers(1, 1 << 40))
+        assert orc.bucket(hi, nb) == (hi * nb) >> 64
+    assert orc.bucket(M64, 7) == 6 and orc.bucket(0, 7) == 0
+
+
+def test_bucket_sizes_follow_binomial(orc):
+    n, b = 200000, 5
+    keys = inputs.u64_keys(n, 3)
+    hi, _ = orc.fingerprint_u64(keys)
+    nb = -(-n // b)
+    buckets = ((hi >> np.uint64(32)).astype(np.float64) * nb / 2.0**32).astype(np.int64)
+    counts = np.bincount(buckets, minlength=nb)
+    # mean exactly n/N; variance of Binomial(n, 1/N) ~ b
+    assert abs(counts.mean() - n / nb) < 1e-9
+    assert 0.9 * b < counts.var() < 1.1 * b
+
+
+# ---------------------------------------------------------------- strategy
+def test_aggregation_constants_match_paper_formulas(orc):
+    for leaf in range(1, 25):
+        s = max(2, math.ceil(0.35 * leaf + 0.5))
+        t = math.ceil(0.21 * leaf + 0.9) if leaf >= 7 else 2
+        # lower aggregation: fanout s at m = s*leaf, units of leaf
+        assert orc.strategy(leaf, s * leaf) == [leaf] * s
+        assert orc.strategy(leaf, s * leaf + 1) == [s * leaf, 1]
+        # upper aggregation: fanout t at m = s*t*leaf, units of s*leaf
+        assert orc.strategy(leaf, s * t * leaf) == [s * leaf] * t
+        # above: binary
+        assert len(orc.strategy(leaf, s * t * leaf + 1)) == 2
+
+
+@pytest.mark.parametrize("leaf", [1, 2, 3, 5, 8, 12, 16, 24])
+def test_strategy_parts_are_units_except_last(orc, leaf):
+    s = max(2, -(-(7 * leaf + 10) // 20))
+    t = -(-(21 * leaf + 90) // 100) if leaf >= 7 else 2
+    for m in list(range(leaf + 1, 3 * s * t * leaf)) + [1000, 2000, 2001, 4097, 65537]:
+        parts = orc.strategy(leaf, m)
+        assert sum(parts) == m and all(p >= 1 for p in parts)
+        if m > s * t * leaf:
+            big = s * t * leaf
+            assert parts[0] == -(-(m // 2) // big) * big
+        else:
+            u = parts[0]
+            assert u % leaf == 0
+            assert all(p == u for p in parts[:-1]) and parts[-1] <= u
+    assert orc.strategy(leaf, leaf) == []
+
+
+def test_strategy_paper_examples(orc):
+    # Sec. 5.4 with l = 8 (s = 4, t = 3) and l = 16 (s = 7, t = 5)
+    assert orc.strategy(8, 100) == [96, 4]
+    assert orc.strategy(8, 32) == [8, 8, 8, 8]
+    assert orc.strategy(8, 96) == [32, 32, 32]
+    assert orc.strategy(16, 2000) == [1120, 880]
+    assert orc.strategy(16, 112) == [16] * 7
+    assert orc.strategy(16, 560) == [112] * 5
+
+
+# ---------------------------------------------------------------- probabilities
+def _count_functions(m, parts):
+    """Number of functions from m keys to [0, m) realising the split (or, for
+    parts=None, bijections), by enumerating all m^m functions."""
+    import itertools
+    bounds = np.cumsum([0] + (parts or []))
+    good = 0
+    for f in itertools.product(range(m), repeat=m):
+        if parts is None:
+            good += len(set(f)) == m
+        else:
+            cnt = [sum(1 for v in f if bounds[t] <= v < bounds[t + 1]) for t in range(len(parts))]
+            good += cnt == parts
+    return Fraction(good, m ** m)
+
+
+@pytest.mark.parametrize("leaf,m", [(5, 2), (5, 3), (5, 4), (5, 5), (6, 6), (2, 3), (2, 4), (5, 6), (3, 6)])
+def test_success_probability_by_enumeration(orc, leaf, m):
+    parts = orc.strategy(leaf, m) or None
+    p = _count_functions(m, parts)
+    assert math.isclose(orc.log_success(leaf, m), math.log(p), rel_tol=1e-12, abs_tol=1e-12)
+
+
+@pytest.mark.parametrize("leaf,m", [(5, 11), (5, 14), (8, 30), (16, 100)])
+def test_multiway_split_probability_monte_carlo(orc, leaf, m):
+    parts = orc.strategy(leaf, m)
+    assert len(parts) >= 3
+    rng = np.random.default_rng(m)
+    trials = 400000
+    v = rng.integers(0, m, size=(trials, m))
+    bounds = np.cumsum([0] + parts)
+    ok = np.ones(trials, dtype=bool)
+    for t in range(len(parts) - 1):
+        ok &= ((v >= bounds[t]) & (v < bounds[t + 1])).sum(axis=1) == parts[t]
+    p = math.exp(orc.log_success(leaf, m))
+    sd = math.sqrt(p * (1 - p) / trials)
+    assert abs(ok.mean() - p) < 5 * sd
+
+
+def _tree_log_prob(orc, leaf, m):
+    if m <= 1:
+        return 0.0
+    total = orc.log_success(leaf, m)
+    for k in orc.strategy(leaf, m):
+        total += _tree_log_prob(orc, leaf, k)
+    return total
+
+
+@pytest.mark.parametrize("leaf", [1, 2, 5, 8, 12, 16, 24])
+def test_invariance_theorem(orc, leaf):
+    # Sec. 5.3: the product of the node probabilities of any tree is m!/m^m
+    for m in list(range(2, 200, 7)) + [1000, 2000, 2345]:
+        want = math.lgamma(m + 1) - m * math.log(m)
+        assert math.isclose(_tree_log_prob(orc, leaf, m), want, rel_tol=1e-10, abs_tol=1e-9)
+
+
+# ---------------------------------------------------------------- Golomb-Rice
+def _expected_len(p, r):
+    """Expected Golomb-Rice code length of a Geometric(p) index with
+    parameter r: r fixed bits plus a unary part of 1/(1 - (1-p)^(2^r)),
+    summed directly over the distribution."""
+    import mpmath
+    q = mpmath.power(1 - p, 2 ** r)
+    # E[floor(K / 2^r)] = sum_{j>=1} P(K >= j 2^r) = sum q^j
+    return r + 1 + q / (1 - q)
+
+
+def _exact_p(orc, leaf, m):
+    import mpmath
+    mpmath.mp.dps = 60
+    logp = mpmath.log(mpmath.factorial(m)) - m * mpmath.log(m)
+    for k in orc.strategy(leaf, m):
+        logp += k * mpmath.log(k) - mpmath.log(mpmath.factorial(k))
+    return mpmath.exp(logp)
+
+
+@pytest.mark.parametrize("leaf", [1, 3, 5, 8, 12, 16, 24])
+def test_golomb_rice_parameter_minimises_expected_length(orc, leaf):
+    pytest.importorskip("mpmath")
+    for m in list(range(2, 120)) + [200, 512, 1000, 2000, 5000]:
+        p = _exact_p(orc, leaf, m)
+        lens = [_expected_len(p, r) for r in range(0, 48)]
+        best = min(range(48), key=lambda r: lens[r])
+        assert orc.golomb_rice(leaf, m) == best, (leaf, m)
+        # Sec. 5.4: the expected unary length is between phi and 1 + phi
+        import mpmath
+        unary = lens[best] - best
+        golden = (1 + mpmath.sqrt(5)) / 2
+        assert golden - 1e-12 <= unary <= 1 + golden + 1e-12
+
+
+def test_golomb_rice_table_has_no_near_ties(orc):
+    # every entry is at least 1e-9 away from a ceiling boundary, so any
+    # correct double evaluation gives the same table
+    for leaf in range(1, 25):
+        for m in list(range(2, 3000)) + list(range(3000, 65536, 97)):
+            x = orc.golomb_rice_x(leaf, m)
+            if x > -1:
+                assert abs(x - round(x)) > 1e-9, (leaf, m, x)
+
+
+def test_golomb_rice_leaf_values(orc):
+    # leaf parameters quoted in the design notes: l = 5, 8, 12, 16
+    assert [orc.golomb_rice(l, l) for l in (5, 8, 12, 16)] == [4, 8, 14, 19]
+
+
+def test_golomb_rice_large_nodes_use_integer_rule(orc):
+    # Sec. 7.2 integer approximation beyond the table (binary split at l = 8)
+    m = 70000
+    parts = orc.strategy(8, m)
+    lam = lambda x: x.bit_length() - 1
+    want = (((len(parts) - 1) * 5 >> 1) + sum(lam(k + (k >> 1)) for k in parts) - lam(m)) >> 1
+    assert orc.golomb_rice(8, m) == want
+    # and it approximates Eq. gr within a couple of bits
+    assert abs(orc.golomb_rice(8, m) - math.ceil(orc.golomb_rice_x(8, m))) <= 2
+
+
+# ---------------------------------------------------------------- searches
+def test_leaf_seed_is_first_bijection(orc):
+    rng = np.random.default_rng(5)
+    for trial in range(60):
+        m = int(rng.integers(2, 8))
+        depth = int(rng.integers(0, 5))
+        lo = rng.integers(0, 1 << 63, size=m, dtype=np.int64).astype(np.uint64) * np.uint64(2) + np.uint64(trial & 1)
+        i = orc.leaf_seed(lo, depth)
+        vals = lambda j: sorted(orc.phi(int(x), depth, j, m) for x in lo)
+        assert vals(i) == list(range(m))
+        for j in range(i):
+            assert vals(j) != list(range(m))
+
+
+def test_split_seed_is_first_split(orc):
+    rng = np.random.default_rng(6)
+    for leaf, m in [(5, 7), (5, 12), (8, 20), (8, 100), (2, 9), (1, 6), (16, 40)]:
+        parts = orc.strategy(leaf, m)
+        bounds = np.cumsum([0] + parts)
+        for depth in (0, 3):
+            lo = rng.integers(0, 1 << 63, size=m, dtype=np.int64).astype(np.uint64)
+            i = orc.split_seed(lo, leaf, depth)
+
+            def counts(j):
+                v = [orc.phi(int(x), depth, j, m) for x in lo]
+                return [sum(1 for y in v if bounds[t] <= y < bounds[t + 1]) for t in range(len(parts))]
+            assert counts(i) == parts
+            for j in range(i):
+                assert counts(j) != parts
+
+
+def _geometric_chi2(seeds, p, nbins=12):
+    """Chi-square statistic of seeds against Geometric(p) on quantile bins."""
+    seeds = np.asarray(seeds)
+    # bin edges at geometric quantiles
+    qs = np.linspace(0, 1, nbins + 1)[1:-1]
+    edges = np.unique(np.ceil(np.log1p(-qs) / np.log1p(-p)).astype(np.int64))
+    edges = np.concatenate([[0], edges, [np.iinfo(np.int64).max]])
+    obs = np.array([((seeds >= a) & (seeds < b)).sum() for a, b in zip(edges[:-1], edges[1:])])
+    cdf = lambda k: 0.0 if k <= 0 else 1 - (1 - p) ** min(k, 1e18)
+    exp = np.array([(cdf(b) - cdf(a)) * len(seeds) for a, b in zip(edges[:-1], edges[1:])])
+    return float(((obs - exp) ** 2 / exp).sum()), len(obs) - 1
+
+
+@pytest.mark.parametrize("kind,leaf,m,samples", [
+    ("leaf", 5, 5, 3000), ("leaf", 8, 8, 800), ("leaf", 5, 3, 3000),
+    ("split", 8, 100, 600), ("split", 5, 14, 2000), ("split", 8, 32, 800), ("split", 16, 112, 60),
+])
+def test_seed_distribution_is_geometric(orc, kind, leaf, m, samples):
+    """Sec. 5.1 / 5.2: with a fully random family the first success is
+    Geometric(p) with p from Eq. probsplit or m!/m^m."""
+    from scipy.stats import chi2
+    rng = np.random.default_rng(1000 + m)
+    p = math.exp(orc.log_success(leaf, m))
+    seeds = []
+    for k in range(samples):
+        lo = rng.integers(0, 1 << 63, size=m, dtype=np.int64).astype(np.uint64) << np.uint64(1)
+        lo |= np.uint64(k & 1)
+        depth = k % 4
+        seeds.append(orc.leaf_seed(lo, depth) if kind == "leaf" else orc.split_seed(lo, leaf, depth))
+    stat, dof = _geometric_chi2(seeds, p)
+    assert chi2.sf(stat, dof) > 1e-4, (stat, dof, np.mean(seeds), 1 / p - 1)
+    mean = np.mean(seeds)
+    assert abs(mean - (1 - p) / p) < 5 * math.sqrt(1 - p) / p / math.sqrt(samples)
+
+
+def test_leaf_trials_grow_by_about_e(orc):
+    # Sec. 8: construction time grows by about e per unit of leaf size
+    ratios = [math.exp(orc.log_success(l, l) - orc.log_success(l + 1, l + 1)) for l in range(5, 20)]
+    assert all(2.2 < r < 2.8 for r in ratios)
+
+
+def test_depths_use_independent_functions(orc):
+    rng = np.random.default_rng(9)
+    same = 0
+    for _ in range(300):
+        lo = rng.integers(0, 1 << 63, size=5, dtype=np.int64).astype(np.uint64)
+        same += orc.leaf_seed(lo, 0) == orc.leaf_seed(lo, 1)
+    # independent geometric(p=0.046) pairs coincide with probability ~ p/(2-p)
+    assert same < 30
+
+
+# ---------------------------------------------------------------- whole structures
+@pytest.mark.parametrize("leaf,b,n", [(5, 5, 100000), (8, 100, 30000), (1, 1, 500), (1, 7, 777), (2, 3, 1000),
+                                      (12, 9, 3000), (3, 1000, 5000), (24, 1, 50), (16, 40, 120),
+                                      (8, 100, 1), (8, 100, 2), (5, 5, 0), (7, 65535, 2000)])
+def test_oracle_builds_minimal_perfect_hash(orc, leaf, b, n):
+    keys = inputs.u64_keys(n, 42 + n)
+    blob = orc.build_u64(keys, leaf, b)
+    h = orc.header(blob)
+    assert h["n"] == n and h["nbuckets"] == -(-n // b)
+    out = orc.lookup_u64(blob, keys)
+    assert np.array_equal(np.sort(out), np.arange(n, dtype=np.uint64))
+
+
+def test_oracle_thread_count_does_not_change_bytes(orc):
+    keys = inputs.u64_keys(50000, 4)
+    a = orc.build_u64(keys, 8, 100, threads=1)
+    b = orc.build_u64(keys, 8, 100, threads=7)
+    assert np.array_equal(a, b)
+
+
+def test_oracle_result_depends_only_on_the_key_set(orc):
+    keys = inputs.u64_keys(20000, 8)
+    a = orc.build_u64(keys, 5, 5)
+    b = orc.build_u64(keys[np.random.default_rng(0).permutation(keys.shape[0])], 5, 5)
+    assert np.array_equal(a, b)
+
+
+def test_duplicate_and_invalid_inputs(orc):
+    keys = inputs.u64_keys(1000, 1)
+    keys[10] = keys[500]
+    with pytest.raises(orc.OracleError) as e:
+        orc.build_u64(keys, 5, 5)
+    assert e.value.code == orc.E_DUPLICATE
+    for leaf, b in [(0, 5), (25, 5), (5, 0), (5, 65536)]:
+        with pytest.raises(orc.OracleError) as e:
+            orc.build_u64(inputs.u64_keys(10, 1), leaf, b)
+        assert e.value.code == orc.E_INVALID
+
+
+def test_byte_keys_structure(orc):
+    bk = inputs.byte_keys(20000, 1)
+    blob = orc.build_bytes(bk.data, bk.offsets, 8, 100)
+    out = orc.lookup_bytes(blob, bk.data, bk.offsets)
+    assert np.array_equal(np.sort(out), np.arange(bk.n, dtype=np.uint64))
+    hi, lo = orc.fingerprint_bytes(bk.data, bk.offsets)
+    assert np.array_equal(orc.build_fingerprints(hi, lo, 8, 100), blob)
+
+
+def test_nonmember_lookups_stay_in_bucket_range(orc):
+    keys = inputs.u64_keys(5000, 12)
+    blob = orc.build_u64(keys, 8, 100)
+    others = inputs.splitmix64(999, 5000)
+    out = orc.lookup_u64(blob, others)
+    assert np.array_equal(out, orc.lookup_u64(blob, others))
+    hi, _ = orc.fingerprint_u64(others)
+    nb = orc.header(blob)["nbuckets"]
+    for i in range(0, 5000, 97):
+        b = orc.bucket(int(hi[i]), nb)
+        s0, _ = orc.bucket_info(blob, b)
+        s1, _ = orc.bucket_info(blob, b + 1)
+        assert s0 <= out[i] <= max(s0, s1 - 1) if s1 > s0 else out[i] == s0
+
+
+# ---------------------------------------------------------------- encoding
+def _expected_tree_bits_per_key(orc, leaf, b, mmax=None):
+    """Sec. 5.4 model: expected Golomb-Rice bits of a tree of size m is the sum
+    over its nodes of r + 1/(1 - (1-p)^(2^r)); bucket sizes are Poisson(b)."""
+    memo = {}
+
+    def tree(m):
+        if m <= 1:
+            return 0.0
+        if m in memo:
+            return memo[m]
+        p = math.exp(orc.log_success(leaf, m))
+        r = orc.golomb_rice(leaf, m)
+        v = r + 1.0 / (1.0 - (1.0 - p) ** (2 ** r))
+        for k in orc.strategy(leaf, m):
+            v += tree(k)
+        memo[m] = v
+        return v
+    mmax = mmax or int(b + 12 * math.sqrt(b) + 20)
+    tot = 0.0
+    for m in range(0, mmax):
+        pm = math.exp(-b + m * math.log(b) - math.lgamma(m + 1)) if m else math.exp(-b)
+        tot += pm * tree(m)
+    return tot / b
+
+
+@pytest.mark.parametrize("leaf,b,n", [(5, 5, 300000), (8, 100, 1000000), (12, 100, 200000), (8, 5, 300000)])
+def test_tree_bits_match_golomb_rice_model(orc, leaf, b, n):
+    keys = inputs.u64_keys(n, 77)
+    blob = orc.build_u64(keys, leaf, b, threads=8)
+    got = orc.tree_bits_per_key(blob)
+    want = _expected_tree_bits_per_key(orc, leaf, b)
+    assert abs(got - want) < 0.02, (got, want)
+
+
+@pytest.mark.parametrize("row", [r for r in _golden_rows("paper_bits_per_key.txt") if int(r[0]) <= 12])
+def test_bits_per_key_match_paper(orc, row):
+    leaf, b, _n, want = int(row[0]), int(row[1]), int(row[2]), float(row[3])
+    n = 1000000 if leaf <= 8 else 200000  # bits/key barely depends on n (Sec. 8)
+    keys = inputs.u64_keys(n, 5)
+    blob = orc.build_u64(keys, leaf, b, threads=8)
+    assert abs(orc.bits_per_key(blob) - want) < 0.05, (orc.bits_per_key(blob), want)
+
+
+def test_decoded_seeds_equal_per_bucket_search(orc):
+    n, leaf, b = 20000, 8, 100
+    keys = inputs.u64_keys(n, 21)
+    blob = orc.build_u64(keys, leaf, b)
+    hi, lo = orc.fingerprint_u64(keys)
+    nb = orc.header(blob)["nbuckets"]
+    bk = np.array([orc.bucket(int(h), nb) for h in hi])
+    for bucket in range(0, nb, 17):
+        seeds = orc.bucket_seeds(lo[bk == bucket], leaf)
+        assert orc.decode_bucket(blob, bucket) == seeds
+
+
+def test_elias_fano_round_trip(orc):
+    n, leaf, b = 100000, 5, 5  # 20000 buckets: spans two 2^14 anchors
+    keys = inputs.u64_keys(n, 31)
+    blob = orc.build_u64(keys, leaf, b)
+    h = orc.header(blob)
+    hi, lo = orc.fingerprint_u64(keys)
+    nb = h["nbuckets"]
+    counts = np.bincount(np.array([orc.bucket(int(x), nb) for x in hi]), minlength=nb)
+    prefix = np.concatenate([[0], np.cumsum(counts)])
+    fixed = {}
+    offsets = [0]
+    for i in range(nb):
+        m = int(counts[i])
+        if m not in fixed:
+            fixed[m] = orc.skip(leaf, m)
+        seeds = orc.decode_bucket(blob, i)
+        assert len(seeds) == fixed[m][1]
+        # code lengths from the decoded indices: fixed bits + unary (i >> r) + 1
+        length = fixed[m][0]
+        stack = [m]
+        sizes = []
+        while stack:
+            sz = stack.pop()
+            if sz < 2:
+                continue
+            sizes.append(sz)
+            stack.extend(reversed(orc.strategy(leaf, sz)))
+        for sz, s in zip(sizes, seeds):
+            length += (s >> orc.golomb_rice(leaf, sz)) + 1
+        offsets.append(offsets[-1] + length)
+    assert offsets[-1] == h["tree_bits"]
+    for i in list(range(0, nb + 1, 7)) + [nb]:
+        s, o = orc.bucket_info(blob, i)
+        assert s == prefix[i] and o == offsets[i]
+
+
+def test_inventory_select_equals_linear_select(orc):
+    keys = inputs.u64_keys(90000, 3)
+    blob = orc.build_u64(keys, 5, 5)
+    nb = orc.header(blob)["nbuckets"]
+    for lst in (0, 1):
+        for rank in list(range(0, 600)) + list(range(16000, 16800, 3)) + [nb - 1, nb]:
+            assert orc.select_inventory(blob, lst, rank) == orc.select_linear(blob, lst, rank)
+
+
+def test_inventory_overflow_entries_are_skipped(orc):
+    """A 16-bit inventory entry that did not fit holds 0xFFFF; select must
+    fall back to an earlier entry and still find every one."""
+    keys = inputs.u64_keys(90000, 3)
+    blob = orc.build_u64(keys, 5, 5)
+    lay = orc.layout(blob)
+    subs = blob[lay["subs"]:].view(np.uint16)
+    for e in (2 * 3, 2 * 3 + 1, 2 * 70, 2 * 65 + 1, 2 * 66 + 1):
+        subs[e] = 0xFFFF
+    nb = orc.header(blob)["nbuckets"]
+    for lst in (0, 1):
+        for rank in list(range(700, 1100)) + list(range(16600, 17100)) + [nb]:
+            assert orc.select_inventory(blob, lst, rank) == orc.select_linear(blob, lst, rank)
