@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""RecSplit construction + lookup benchmark (one JSON line on rank 0).
+
+Workload (default): 10^7 random byte-string keys of 8..32 bytes (seed 1),
+leaf size l = 8, bucket size b = 100, then 10^8 uniform lookups drawn from the
+key set.  One step = one build of the whole structure from keys resident in
+HBM plus the 10^8 lookups.  `value` is keys built per second (build time),
+`lookup` the queries answered per second; `e2e` repeats the build through the
+C ABI from pinned host buffers (host->device copy and the read-back of the
+structure inside the timed region).
+
+--impl reference times the CPU oracle (the plain C implementation the tests
+compare against) on a bounded sample of the same workload.
+
+With torchrun (N > 1) every rank builds its own replica of the workload (the
+path has no exchange step on one GPU per box: replicas only); `value` sums
+the keys of all ranks over the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build keys/s and lookup Mqueries/s at ℓ=8,b=100 vs INT/HBM roofline; serve p50/p99"
+OPS_PER_LEAF_EVAL = 17   # 32-bit instructions of one leaf evaluation (hash, range, one-hot OR)
+OPS_PER_SPLIT_EVAL = 20  # 32-bit instructions of one split evaluation (hash, range, part, packed count)
+SM_COUNT = 152
+LANES_PER_SM_CLK = 128   # 4 sub-partitions x 1 warp instruction (32 lanes) per clock
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--queries", type=int, default=100_000_000)
+    ap.add_argument("--leaf", type=int, default=8)
+    ap.add_argument("--bucket", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(a):
+    return {"workload": f"{a.n} random byte-string keys (8-32 B, seed 1), l={a.leaf}, b={a.bucket}, "
+                        f"{a.queries} uniform member lookups",
+            "n": a.n, "leaf_size": a.leaf, "bucket_size": a.bucket, "queries": a.queries,
+            "key_type": "bytes", "l2": "inputs larger than L2 (keys ~280 MB, queries ~2.8 GB)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def traffic_from_profiles(kernel_tag):
+    """DRAM bytes per launch recorded by an ncu capture summary, if the kernel
+    source has not changed since (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    src = os.path.join(ROOT, "paper_1910_06416_gb300", "csrc", "search.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("source_sha256_16") != sha:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(a, keys_np):
+    """The oracle (plain C, all host cores) on a bounded sample of the workload."""
+    from oracle import oracle
+    from paper_1910_06416_gb300 import inputs
+    threads = os.cpu_count() or 1
+    ns = min(a.n, 2_000_000)
+    sub = inputs.ByteKeys(keys_np.data[:int(keys_np.offsets[ns])], keys_np.offsets[:ns + 1])
+    t0 = time.perf_counter()
+    oracle.build_bytes(sub.data, sub.offsets, a.leaf, a.bucket, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": ns / dt, "unit": "keys/s", "cores": threads, "kind": "oracle",
+            "sample": f"oracle build of the first {ns} keys of the workload (same l, b; {threads} threads), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_1910_06416_gb300 import inputs
+    threads = os.cpu_count() or 1
+    ns = min(a.n, 1_000_000)
+    keys = inputs.byte_keys(ns, 1)
+    times = []
+    for step in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        oracle.build_bytes(keys.data, keys.offsets, a.leaf, a.bucket, threads=threads)
+        if step >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    value = ns * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": dict(workload_config(a), sample_keys=ns),
+            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": threads, "kind": "oracle",
+                             "sample": f"oracle build of {ns} keys of the workload per step ({threads} threads)"},
+            "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+
+    from paper_1910_06416_gb300 import build as lib_build, inputs
+    import paper_1910_06416_gb300.recsplit as rs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        lib_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    rs.lib()
+
+    keys = inputs.byte_keys(a.n, 1)
+    data = torch.from_numpy(keys.data).to(dev)
+    offs = torch.from_numpy(keys.offsets.view(np.int64)).to(dev)
+    idx = inputs.query_indices(a.n, a.queries, 1)
+    qdata, qoffs = inputs.device_byte_queries(keys, idx, device=dev)
+    del idx
+    qout = torch.empty(a.queries, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    rs.recsplit_set_profiling(True)
+
+    def step():
+        b0, b1, l1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        b0.record(stream)
+        h = rs.recsplit_build_bytes(data, offs, a.leaf, a.bucket, stream.cuda_stream)
+        b1.record(stream)
+        rs.recsplit_lookup_bytes(h, qdata, qoffs, qout, stream.cuda_stream)
+        l1.record(stream)
+        prof = rs.recsplit_last_profile()
+        return h, (b0, b1, l1), prof
+
+    for _ in range(a.warmup):
+        h, _, _ = step()
+        torch.cuda.synchronize()
+        rs.recsplit_free(h)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = rs.recsplit_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    records = []
+    for _ in range(a.steps):
+        h, ev, prof = step()
+        records.append((h, ev, prof))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = rs.recsplit_launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    stats = rs.recsplit_stats(records[-1][0])
+    for h, _, _ in records:
+        rs.recsplit_free(h)
+
+    total_ms = t_start.elapsed_time(t_end)
+    build_ms = [ev[0].elapsed_time(ev[1]) for _, ev, _ in records]
+    look_ms = [ev[1].elapsed_time(ev[2]) for _, ev, _ in records]
+    profs = [p for _, _, p in records]
+    if world > 1:
+        t = torch.tensor([total_ms, sum(build_ms), sum(look_ms)], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, sb, sl = (float(x) for x in t.tolist())
+    else:
+        sb, sl = sum(build_ms), sum(look_ms)
+    value = world * a.n * a.steps / (sb / 1000.0)
+    lookup_qps = world * a.queries * a.steps / (sl / 1000.0)
+
+    # roofline of the dominant kernel (integer issue bound; no tensor cores)
+    leaf_ms = sum(p["ms_leaf"] for p in profs) / len(profs)
+    split_ms = sum(p["ms_split"] for p in profs) / len(profs)
+    leaf_ops = profs[-1]["leaf_evals"] * OPS_PER_LEAF_EVAL
+    split_ops = profs[-1]["split_evals"] * OPS_PER_SPLIT_EVAL
+    peak_ops = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    if leaf_ms >= split_ms:
+        kernel, achieved = "leaf_search", leaf_ops / (leaf_ms / 1000.0)
+    else:
+        kernel, achieved = "split_search", split_ops / (split_ms / 1000.0)
+    tag = f"{kernel}_strings_n{a.n}_l{a.leaf}_b{a.bucket}"
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic_from_profiles(tag),
+                "peak_source": "152 SMs x 128 lanes/clk x 2070 MHz (issue-limited 32-bit integer instructions)",
+                "ops_per_eval": OPS_PER_LEAF_EVAL if kernel == "leaf_search" else OPS_PER_SPLIT_EVAL}
+    lookup_bytes = int(qdata.numel()) + 8 * (a.queries + 1) + 8 * a.queries
+    look_gbs = lookup_bytes / (sl / a.steps / 1000.0) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if rank == 0:
+        hdata = torch.from_numpy(keys.data).pin_memory()
+        hoffs = torch.from_numpy(keys.offsets.view(np.int64)).pin_memory()
+        ts = []
+        blob_bytes = 0
+        for k in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = rs.recsplit_build_bytes(hdata, hoffs, a.leaf, a.bucket, stream.cuda_stream)
+            blob = rs.recsplit_serialize(h)
+            t1 = time.perf_counter()
+            rs.recsplit_free(h)
+            blob_bytes = blob.nbytes
+            ts.append(t1 - t0)
+        e2e = {"value": a.n / min(ts), "unit": "keys/s",
+               "h2d_bytes_per_step": int(hdata.numel() + 8 * hoffs.numel()), "d2h_bytes_per_step": int(blob_bytes)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": dict(workload_config(a), parallelism=f"replicas{world}"),
+                "lookup": {"value": lookup_qps, "unit": "queries/s",
+                           "hbm": {"achieved": look_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": look_gbs / hbm_peak, "bytes_per_query": lookup_bytes / a.queries}},
+                "build_ms": statistics.median(build_ms), "lookup_ms": statistics.median(look_ms),
+                "phases_ms": {k: statistics.median(p[k] for p in profs)
+                              for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")},
+                "work": {k: profs[-1][k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes",
+                                                   "leaf_trials", "leaf_evals")},
+                "bits_per_key": stats["bits_per_key"], "roofline": roofline, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks}
+        if not a.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(a, keys)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,157 @@
+/*
+ * recsplit.h -- C ABI of the GB300 (sm_103a) RecSplit library.
+ *
+ * RecSplit (Esposito, Mueller Graf, Vigna, "RecSplit: Minimal Perfect Hashing
+ * via Recursive Splitting") maps a set of n distinct keys one-to-one onto
+ * [0, n).  Construction hashes every key to a 128-bit signature, distributes
+ * the signatures into ceil(n / b) buckets, and per bucket searches by brute
+ * force, top-down, for the first hash function that splits the keys into parts
+ * of prescribed sizes, until parts of at most leaf_size keys remain, where it
+ * searches for the first function that is a bijection (Sec. 4, Sec. 5).  The
+ * found indices are stored with Golomb-Rice codes (Sec. 6.2), and the bucket
+ * prefix sums and bit offsets with a double Elias-Fano list (Sec. 6.3, 7.4).
+ *
+ * Conventions for every call:
+ *  - Pointers to keys, queries and outputs may point to host memory or to
+ *    device memory of the current CUDA device; the library detects which and
+ *    copies host buffers itself (inside the call, on `stream`).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Build
+ *    returns once the structure is complete on the device; lookups with
+ *    device outputs return as soon as the work is queued on `stream`, lookups
+ *    with host outputs return after the results have been copied back.
+ *  - The caller owns every buffer it passes; the library owns a structure
+ *    from the build (or deserialize) that creates it until recsplit_free.
+ *  - Every int-returning call returns RECSPLIT_OK (0) or a negative error
+ *    code; recsplit_strerror gives its text and recsplit_last_error the
+ *    message of the most recent failure on the calling host thread.
+ *  - Results do not depend on the order of the keys, only on the key set.
+ */
+#ifndef RECSPLIT_H
+#define RECSPLIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RECSPLIT_OK 0
+#define RECSPLIT_E_INVALID (-1)      /* bad argument: leaf_size outside [1,24], bucket_size outside
+                                        [1,65535], n >= 2^32, NULL pointer, bad serialized data */
+#define RECSPLIT_E_DUPLICATE (-2)    /* two keys share their 64-bit lower signature half (for
+                                        64-bit keys: the key set has a repeated key) */
+#define RECSPLIT_E_SEARCH_LIMIT (-4) /* a split or bijection search passed 2^36 trials */
+#define RECSPLIT_E_NOMEM (-5)        /* device or host allocation failed */
+#define RECSPLIT_E_CUDA (-6)         /* a CUDA runtime call failed */
+
+/* Opaque handle to a built structure resident in device memory. */
+typedef struct recsplit recsplit_t;
+
+/* Summary of a structure (recsplit_stats). */
+typedef struct recsplit_stats {
+  uint64_t n;             /* number of keys                                   */
+  uint32_t leaf_size;     /* l                                                */
+  uint32_t bucket_size;   /* b                                                */
+  uint64_t num_buckets;   /* N = ceil(n / b)                                  */
+  uint64_t tree_bits;     /* T: bits of all Golomb-Rice codes                 */
+  uint64_t total_bits;    /* size of the serialized structure in bits         */
+  uint64_t max_bucket;    /* largest bucket                                   */
+  uint64_t num_codes;     /* number of stored split/bijection indices         */
+  double tree_bits_per_key;
+  double bits_per_key;    /* total_bits / n                                   */
+} recsplit_stats_t;
+
+/* Build from n 64-bit keys (Sec. 4).  keys: n uint64 values, host or device.
+ * leaf_size: l in [1, 24] (Sec. 5.4 bounds leaves by 24); bucket_size: b in
+ * [1, 65535].  On success *out receives a new structure.  Fails with
+ * RECSPLIT_E_DUPLICATE on repeated keys.  n = 0 gives an empty structure. */
+int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size,
+                       void* stream, recsplit_t** out);
+
+/* The same for n byte strings: key i is bytes[offsets[i] .. offsets[i+1]),
+ * offsets has n + 1 non-decreasing entries (offsets[0] may be non-zero);
+ * both arrays host or device (both in the same kind of memory). */
+int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
+                         uint32_t bucket_size, void* stream, recsplit_t** out);
+
+/* recsplit_build_u64 under the short name of the construction call. */
+int recsplit_build(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
+                   recsplit_t** out);
+
+/* Lookup of q 64-bit keys (Sec. 4): out[i] = the index in [0, n) of keys[i]
+ * for keys of the set; for other keys a deterministic value in [0, n]
+ * (Sec. 1 allows any value).  keys and out: host or device. */
+int recsplit_lookup_u64(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
+
+/* Lookup of q byte strings, laid out as in recsplit_build_bytes. */
+int recsplit_lookup_bytes(const recsplit_t* h, const uint8_t* bytes, const uint64_t* offsets, uint64_t q,
+                          uint64_t* out, void* stream);
+
+/* recsplit_lookup_u64 under the short name of the lookup call. */
+int recsplit_lookup(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
+
+/* Serialized form (little-endian 64-bit words; header, Golomb-Rice bit
+ * array, Elias-Fano lists).  With buf == NULL only *len (bytes) is set;
+ * otherwise cap must be at least that size.  Synchronises with the device. */
+int recsplit_serialize(const recsplit_t* h, void* buf, size_t cap, size_t* len);
+
+/* Structure from a serialized buffer in host memory (copied). */
+int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t** out);
+
+/* Summary figures of a structure (host only, no device work). */
+int recsplit_stats(const recsplit_t* h, recsplit_stats_t* st);
+
+/* Releases a structure (NULL is allowed). */
+void recsplit_free(recsplit_t* h);
+
+/* Text of an error code (static storage). */
+const char* recsplit_strerror(int code);
+
+/* Message of the last failure on the calling host thread ("" if none). */
+const char* recsplit_last_error(void);
+
+/* Per-phase device timing of a build (CUDA events on the build's stream)
+ * and the algorithmic work of its searches.  Recorded only while profiling
+ * is on (recsplit_set_profiling); phases follow the construction order:
+ * signatures + bucket histogram (Sec. 6.1), grouping (prefix sums, scatter),
+ * split searches (Sec. 5.1), leaf searches (Sec. 5.2), encoding (Golomb-Rice
+ * codes and Elias-Fano lists, Sec. 6.2-6.3). */
+typedef struct recsplit_profile {
+  double ms_signature;
+  double ms_group;
+  double ms_split;
+  double ms_leaf;
+  double ms_encode;
+  double ms_total;
+  uint64_t split_nodes;   /* split nodes searched                               */
+  uint64_t split_trials;  /* sum over split nodes of (found index + 1)          */
+  uint64_t split_evals;   /* sum over split nodes of (found index + 1) * keys   */
+  uint64_t leaf_nodes;
+  uint64_t leaf_trials;
+  uint64_t leaf_evals;
+  uint32_t launches;      /* kernels launched by the build                      */
+  uint32_t split_levels;  /* launches of the split search (one per tree level)  */
+} recsplit_profile_t;
+
+/* Turns per-build profiling on (non-zero) or off (0) for the calling host
+ * thread.  Profiling adds events and one reduction kernel per build. */
+int recsplit_set_profiling(int enabled);
+
+/* Profile of the last successful build on the calling host thread. */
+int recsplit_last_profile(recsplit_profile_t* out);
+
+/* Kernels launched by the library on the calling host thread so far. */
+uint64_t recsplit_launch_count(void);
+
+/* Golomb-Rice parameters of nodes of 0 .. m_hi keys for leaf size l
+ * (Sec. 5.4 Eq. gr with the probabilities of Sec. 5.1 / 5.2, and the integer
+ * rule of Sec. 7.2 from 2^16 keys on): out[m] for m in [0, m_hi], host
+ * memory, m_hi + 1 entries.  Host-only; for inspection and tests. */
+int recsplit_golomb_rice_params(uint32_t leaf_size, uint64_t m_hi, uint8_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECSPLIT_H */

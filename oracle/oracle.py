@@ -21,7 +21,7 @@ LIB = os.path.join(LIBDIR, "liboracle.so")
 
 E_INVALID, E_DUPLICATE, E_SEARCH_LIMIT, E_NOMEM = -1, -2, -4, -5
 HEADER_FIELDS = ("magic", "n", "leaf", "bucket_size", "nbuckets", "tree_bits", "mmax", "beta",
-                 "delta_a", "delta_b", "low_a", "low_b", "upper_a_bits", "upper_b_bits", "words")
+                 "delta_a", "delta_b", "low_a", "low_b", "upper_a_bits", "upper_b_bits", "words", "codes")
 
 _lock = threading.Lock()
 _lib = None

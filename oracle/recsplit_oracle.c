@@ -608,6 +608,7 @@ int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, u
   h[11] = (uint64_t)lb;
   h[12] = ua;
   h[13] = ub;
+  h[15] = ncodes;
   orc_layout L;
   orc_layout_of(h, &L);
   h[14] = L.total;

@@ -1,0 +1,322 @@
+// C ABI entry points (include/recsplit.h): argument checks, host/device
+// buffer staging, serialization and error reporting.
+#include <cstring>
+#include <string>
+
+#include "common.h"
+
+namespace rs {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? RECSPLIT_E_NOMEM : RECSPLIT_E_CUDA;
+}
+
+static thread_local bool g_profiling = false;
+static thread_local recsplit_profile_t g_profile = {};
+static thread_local bool g_have_profile = false;
+static thread_local uint64_t g_launches = 0;
+
+bool profiling_enabled() { return g_profiling; }
+void store_profile(const recsplit_profile_t& p) {
+  g_profile = p;
+  g_have_profile = true;
+}
+void count_launch(uint32_t k) { g_launches += k; }
+uint64_t launch_mark() { return g_launches; }
+uint32_t launches_since(uint64_t mark) { return static_cast<uint32_t>(g_launches - mark); }
+
+namespace {
+
+bool on_device(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Device copy of a host buffer (or the device pointer itself).
+struct Staged {
+  void* dev = nullptr;
+  bool owned = false;
+  cudaStream_t s = nullptr;
+  ~Staged() {
+    if (owned) cudaFreeAsync(dev, s);
+  }
+  int from(const void* p, size_t bytes, bool device, cudaStream_t stream) {
+    s = stream;
+    if (device || bytes == 0) {
+      dev = const_cast<void*>(p);
+      return RECSPLIT_OK;
+    }
+    if (cudaMallocAsync(&dev, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RECSPLIT_E_NOMEM, "device allocation for staging host input failed");
+    }
+    owned = true;
+    RS_CUDA(cudaMemcpyAsync(dev, p, bytes, cudaMemcpyHostToDevice, s));
+    return RECSPLIT_OK;
+  }
+};
+
+int check_build_args(uint64_t n, uint32_t leaf, uint32_t bucket_size, recsplit_t** out) {
+  if (!out) return fail(RECSPLIT_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (leaf < 1 || leaf > kMaxLeaf) return fail(RECSPLIT_E_INVALID, "leaf_size must be in [1, 24]");
+  if (bucket_size < 1 || bucket_size > kMaxBucket) return fail(RECSPLIT_E_INVALID, "bucket_size must be in [1, 65535]");
+  if (n >= (1ull << 32)) return fail(RECSPLIT_E_INVALID, "n must be below 2^32");
+  return RECSPLIT_OK;
+}
+
+Handle* as_handle(recsplit_t* h) { return reinterpret_cast<Handle*>(h); }
+const Handle* as_handle(const recsplit_t* h) { return reinterpret_cast<const Handle*>(h); }
+
+}  // namespace
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
+                       recsplit_t** out) {
+  int rc = check_build_args(n, leaf_size, bucket_size, out);
+  if (rc) return rc;
+  if (n && !keys) return fail(RECSPLIT_E_INVALID, "keys is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staged k;
+  if ((rc = k.from(keys, n * sizeof(uint64_t), n && on_device(keys), s))) return rc;
+  KeyInput in;
+  in.u64 = static_cast<const uint64_t*>(k.dev);
+  in.n = n;
+  Handle* h = nullptr;
+  if ((rc = build_structure(in, leaf_size, bucket_size, s, &h))) return rc;
+  *out = reinterpret_cast<recsplit_t*>(h);
+  return RECSPLIT_OK;
+}
+
+int recsplit_build(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
+                   recsplit_t** out) {
+  return recsplit_build_u64(keys, n, leaf_size, bucket_size, stream, out);
+}
+
+int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
+                         uint32_t bucket_size, void* stream, recsplit_t** out) {
+  int rc = check_build_args(n, leaf_size, bucket_size, out);
+  if (rc) return rc;
+  if (n && (!offsets || !bytes)) return fail(RECSPLIT_E_INVALID, "bytes or offsets is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool dev = n && on_device(offsets);
+  if (n && on_device(bytes) != dev) return fail(RECSPLIT_E_INVALID, "bytes and offsets must both be host or device");
+  Staged b, o;
+  if (n && !dev) {
+    const uint64_t total = offsets[n];
+    for (uint64_t i = 0; i < n; i++)
+      if (offsets[i + 1] < offsets[i]) return fail(RECSPLIT_E_INVALID, "offsets must not decrease");
+    if ((rc = b.from(bytes, total, false, s)) || (rc = o.from(offsets, (n + 1) * sizeof(uint64_t), false, s)))
+      return rc;
+  } else {
+    b.dev = const_cast<uint8_t*>(bytes);
+    o.dev = const_cast<uint64_t*>(offsets);
+  }
+  KeyInput in;
+  in.bytes = static_cast<const uint8_t*>(b.dev);
+  in.offsets = static_cast<const uint64_t*>(o.dev);
+  in.n = n;
+  Handle* h = nullptr;
+  if ((rc = build_structure(in, leaf_size, bucket_size, s, &h))) return rc;
+  *out = reinterpret_cast<recsplit_t*>(h);
+  return RECSPLIT_OK;
+}
+
+static int lookup_common(const recsplit_t* hp, const KeyInput& q_host_or_dev, bool inputs_on_device,
+                         uint64_t* out, void* stream) {
+  const Handle* h = as_handle(hp);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t q = q_host_or_dev.n;
+  int rc;
+  KeyInput q_dev = q_host_or_dev;
+  Staged k, b, o, res;
+  if (!inputs_on_device && q) {
+    if (q_host_or_dev.u64) {
+      if ((rc = k.from(q_host_or_dev.u64, q * sizeof(uint64_t), false, s))) return rc;
+      q_dev.u64 = static_cast<const uint64_t*>(k.dev);
+    } else {
+      const uint64_t total = q_host_or_dev.offsets[q];
+      if ((rc = b.from(q_host_or_dev.bytes, total, false, s)) ||
+          (rc = o.from(q_host_or_dev.offsets, (q + 1) * sizeof(uint64_t), false, s)))
+        return rc;
+      q_dev.bytes = static_cast<const uint8_t*>(b.dev);
+      q_dev.offsets = static_cast<const uint64_t*>(o.dev);
+    }
+  }
+  const bool out_dev = q && on_device(out);
+  uint64_t* d_out = out;
+  if (!out_dev && q) {
+    res.s = s;
+    if (cudaMallocAsync(&res.dev, q * sizeof(uint64_t), s) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RECSPLIT_E_NOMEM, "device allocation for lookup results failed");
+    }
+    res.owned = true;
+    d_out = static_cast<uint64_t*>(res.dev);
+  }
+  if ((rc = lookup_structure(*h, q_dev, d_out, s))) return rc;
+  if (!out_dev && q) {
+    RS_CUDA(cudaMemcpyAsync(out, d_out, q * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    RS_CUDA(cudaStreamSynchronize(s));
+  } else if (!inputs_on_device && q) {
+    // staged inputs are released on the stream; nothing else to wait for
+  }
+  return RECSPLIT_OK;
+}
+
+int recsplit_lookup_u64(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream) {
+  if (!h) return fail(RECSPLIT_E_INVALID, "structure is NULL");
+  if (q && (!keys || !out)) return fail(RECSPLIT_E_INVALID, "keys or out is NULL");
+  KeyInput in;
+  in.u64 = keys;
+  in.n = q;
+  return lookup_common(h, in, q && on_device(keys), out, stream);
+}
+
+int recsplit_lookup(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream) {
+  return recsplit_lookup_u64(h, keys, q, out, stream);
+}
+
+int recsplit_lookup_bytes(const recsplit_t* h, const uint8_t* bytes, const uint64_t* offsets, uint64_t q,
+                          uint64_t* out, void* stream) {
+  if (!h) return fail(RECSPLIT_E_INVALID, "structure is NULL");
+  if (q && (!bytes || !offsets || !out)) return fail(RECSPLIT_E_INVALID, "bytes, offsets or out is NULL");
+  const bool dev = q && on_device(offsets);
+  if (q && on_device(bytes) != dev) return fail(RECSPLIT_E_INVALID, "bytes and offsets must both be host or device");
+  KeyInput in;
+  in.bytes = bytes;
+  in.offsets = offsets;
+  in.n = q;
+  return lookup_common(h, in, dev, out, stream);
+}
+
+int recsplit_serialize(const recsplit_t* hp, void* buf, size_t cap, size_t* len) {
+  if (!hp || !len) return fail(RECSPLIT_E_INVALID, "structure or len is NULL");
+  const Handle* h = as_handle(hp);
+  const size_t bytes = h->layout.total * sizeof(uint64_t);
+  *len = bytes;
+  if (!buf) return RECSPLIT_OK;
+  if (cap < bytes) return fail(RECSPLIT_E_INVALID, "buffer too small");
+  RS_CUDA(cudaDeviceSynchronize());
+  RS_CUDA(cudaMemcpy(buf, h->d_blob, bytes, cudaMemcpyDeviceToHost));
+  return RECSPLIT_OK;
+}
+
+int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t** out) {
+  if (!buf || !out) return fail(RECSPLIT_E_INVALID, "buffer or out is NULL");
+  *out = nullptr;
+  if (len < kHeaderWords * sizeof(uint64_t) || len % 8) return fail(RECSPLIT_E_INVALID, "truncated structure");
+  uint64_t H[kHeaderWords];
+  std::memcpy(H, buf, sizeof(H));
+  if (H[H_MAGIC] != kMagic) return fail(RECSPLIT_E_INVALID, "bad magic");
+  if (H[H_LEAF] < 1 || H[H_LEAF] > kMaxLeaf || H[H_BUCKET] < 1 || H[H_BUCKET] > kMaxBucket ||
+      H[H_N] >= (1ull << 32) || H[H_NB] != (H[H_N] + H[H_BUCKET] - 1) / H[H_BUCKET] || H[H_LOW_A] > 63 ||
+      H[H_LOW_B] > 63 || H[H_MMAX] > H[H_N])
+    return fail(RECSPLIT_E_INVALID, "inconsistent header");
+  const Layout L = layout_of(H);
+  if (L.total != H[H_WORDS] || L.total * sizeof(uint64_t) != len)
+    return fail(RECSPLIT_E_INVALID, "size does not match the header");
+  Tables T;
+  std::string err;
+  int rc = build_tables(static_cast<uint32_t>(H[H_LEAF]), H[H_MMAX], &T, &err);
+  if (rc) return fail(rc, err);
+  Handle* h = new Handle();
+  std::memcpy(h->header, H, sizeof(H));
+  h->layout = L;
+  cudaGetDevice(&h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMalloc(&h->d_blob, len) != cudaSuccess ||
+      cudaMalloc(&h->d_table, T.device_words.size() * sizeof(uint64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->d_blob);
+    delete h;
+    return fail(RECSPLIT_E_NOMEM, "device allocation failed");
+  }
+  if (cudaMemcpyAsync(h->d_blob, buf, len, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_table, T.device_words.data(), T.device_words.size() * sizeof(uint64_t),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "deserialize");
+    cudaFree(h->d_blob);
+    cudaFree(h->d_table);
+    delete h;
+    return rc;
+  }
+  h->ncodes = H[H_CODES];
+  *out = reinterpret_cast<recsplit_t*>(h);
+  return RECSPLIT_OK;
+}
+
+int recsplit_stats(const recsplit_t* hp, recsplit_stats_t* st) {
+  if (!hp || !st) return fail(RECSPLIT_E_INVALID, "structure or stats is NULL");
+  const Handle* h = as_handle(hp);
+  const uint64_t* H = h->header;
+  st->n = H[H_N];
+  st->leaf_size = static_cast<uint32_t>(H[H_LEAF]);
+  st->bucket_size = static_cast<uint32_t>(H[H_BUCKET]);
+  st->num_buckets = H[H_NB];
+  st->tree_bits = H[H_TBITS];
+  st->total_bits = h->layout.total * 64;
+  st->max_bucket = H[H_MMAX];
+  st->num_codes = h->ncodes;
+  st->tree_bits_per_key = H[H_N] ? double(H[H_TBITS]) / double(H[H_N]) : 0.0;
+  st->bits_per_key = H[H_N] ? double(st->total_bits) / double(H[H_N]) : 0.0;
+  return RECSPLIT_OK;
+}
+
+void recsplit_free(recsplit_t* hp) {
+  if (!hp) return;
+  Handle* h = as_handle(hp);
+  cudaFree(h->d_blob);
+  cudaFree(h->d_table);
+  delete h;
+}
+
+const char* recsplit_strerror(int code) {
+  switch (code) {
+    case RECSPLIT_OK: return "success";
+    case RECSPLIT_E_INVALID: return "invalid argument";
+    case RECSPLIT_E_DUPLICATE: return "keys share a signature half (duplicate keys)";
+    case RECSPLIT_E_SEARCH_LIMIT: return "seed search limit reached";
+    case RECSPLIT_E_NOMEM: return "out of memory";
+    case RECSPLIT_E_CUDA: return "CUDA runtime error";
+    default: return "unknown error";
+  }
+}
+
+const char* recsplit_last_error(void) { return g_last_error.c_str(); }
+
+int recsplit_set_profiling(int enabled) {
+  g_profiling = enabled != 0;
+  return RECSPLIT_OK;
+}
+
+int recsplit_last_profile(recsplit_profile_t* out) {
+  if (!out) return fail(RECSPLIT_E_INVALID, "out is NULL");
+  if (!g_have_profile) return fail(RECSPLIT_E_INVALID, "no profiled build on this thread");
+  *out = g_profile;
+  return RECSPLIT_OK;
+}
+
+uint64_t recsplit_launch_count(void) { return g_launches; }
+
+}  // extern "C"

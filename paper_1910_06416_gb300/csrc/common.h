@@ -1,0 +1,164 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/recsplit.h"
+
+namespace rs {
+
+// ---------------------------------------------------------------- format
+constexpr uint64_t kMagic = 0x31544C5053434552ull;  // "RECSPLT1"
+constexpr int kHeaderWords = 16;
+constexpr uint64_t kMaxTrials = 1ull << 36;  // search limit per node
+constexpr int kInvHi = 14;                    // u64 anchor every 2^14 ones
+constexpr int kInvLo = 8;                     // u16 offset every 2^8 ones
+constexpr uint32_t kMaxLeaf = 24;
+constexpr uint32_t kMaxBucket = 65535;
+constexpr int kMaxDepth = 63;
+
+enum HeaderWord : int {
+  H_MAGIC = 0, H_N, H_LEAF, H_BUCKET, H_NB, H_TBITS, H_MMAX, H_BETA,
+  H_DELTA_A, H_DELTA_B, H_LOW_A, H_LOW_B, H_UP_A, H_UP_B, H_WORDS, H_CODES
+};
+
+inline uint64_t words_of_bits(uint64_t bits) { return (bits + 63) >> 6; }
+
+// Word offsets of the sections of a structure, derived from its header.
+struct Layout {
+  uint64_t tree, lower, upper_a, upper_b, anchors, subs, total;
+  uint64_t n_anchor, n_sub;
+};
+Layout layout_of(const uint64_t* header);
+
+// ---------------------------------------------------------------- strategy
+// Sec. 5.4: leaves of at most `leaf` keys; units leaf (lower aggregation)
+// and s*leaf (upper aggregation); binary splits in multiples of s*t*leaf.
+struct Strategy {
+  uint32_t leaf;
+  uint64_t lower;  // s * leaf
+  uint64_t upper;  // s * t * leaf
+};
+Strategy make_strategy(uint32_t leaf);
+
+struct Shape {
+  uint32_t fanout;  // 0 for a leaf (m <= leaf)
+  uint64_t unit;    // size of every part but the last
+  uint64_t last;    // size of the last part
+};
+Shape shape_of(const Strategy& st, uint64_t m);
+
+int golomb_rice_param(const Strategy& st, uint64_t m);
+
+// Per-size tables for node sizes 0 .. mmax.  Device form: four words per size
+//   w0 = fixed_bits(subtree) | codes(subtree) << 32
+//   w1 = unit | fanout << 32 | r << 40
+//   w2 = expected number of trials (1/p rounded up), w3 = 0
+constexpr int kTableWords = 4;
+struct Tables {
+  uint64_t mmax = 0;
+  std::vector<uint8_t> r;
+  std::vector<uint64_t> fixed_bits;
+  std::vector<uint64_t> codes;
+  std::vector<uint64_t> expected_trials;  // 1/p rounded up (search stall detection)
+  std::vector<uint64_t> device_words;     // kTableWords per size
+};
+int build_tables(uint32_t leaf, uint64_t mmax, Tables* out, std::string* err);
+
+// ---------------------------------------------------------------- handle
+struct Handle {
+  uint64_t header[kHeaderWords];
+  Layout layout;
+  uint64_t* d_blob = nullptr;   // serialized structure, device resident
+  uint64_t* d_table = nullptr;  // device_words of the tables
+  uint64_t ncodes = 0;
+  int device = 0;
+};
+
+// Device-side view of a structure, passed by value to lookup kernels.
+struct View {
+  const uint64_t* tree;
+  const uint64_t* lower;
+  const uint64_t* upper_a;
+  const uint64_t* upper_b;
+  const uint64_t* anchors;
+  const uint16_t* subs;
+  const uint64_t* table;  // kTableWords words per size
+  uint64_t nb;
+  uint64_t beta;
+  int64_t delta_a, delta_b;
+  uint32_t low_a, low_b;
+  uint32_t leaf;
+};
+View make_view(const Handle& h);
+
+// ---------------------------------------------------------------- tracing
+bool profiling_enabled();
+void store_profile(const recsplit_profile_t& p);
+void count_launch(uint32_t k = 1);
+uint32_t launches_since(uint64_t mark);
+uint64_t launch_mark();
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define RS_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return rs::cuda_fail(e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- launchers
+// Exclusive scan of `count` uint64 values: out[0..count] with out[count] =
+// total.  `in` and `out` may alias.  Temporary storage comes from the
+// stream-ordered allocator.
+int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t count, cudaStream_t s);
+
+// Kinds of key input.
+struct KeyInput {
+  const uint64_t* u64 = nullptr;   // 64-bit keys, or
+  const uint8_t* bytes = nullptr;  // byte strings with
+  const uint64_t* offsets = nullptr;
+  uint64_t n = 0;
+};
+
+int build_structure(const KeyInput& in, uint32_t leaf, uint32_t bucket_size, cudaStream_t s, Handle** out);
+int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s);
+
+// Search launchers (search.cu).
+struct Node {
+  uint32_t start;  // first key (index into the key array of its depth parity)
+  uint32_t m;      // keys
+  uint32_t slot;   // code slot of this node (preorder within its bucket)
+  uint32_t depth;  // depth in the tree, root = 0
+};
+
+struct SearchArgs {
+  uint64_t* keys[2];         // key arrays (x ^ x >> 30) by depth parity
+  uint64_t* seeds;           // one per code slot
+  uint32_t* sizes;           // node size per code slot
+  const uint64_t* table;     // device tables
+  Node* split_in;            // split nodes of this level
+  uint32_t* split_in_count;
+  Node* split_out;           // split nodes of the next level
+  uint32_t* split_out_count;
+  Node* leaves_full;         // leaves of exactly `leaf` keys
+  uint32_t* leaves_full_count;
+  Node* leaves_part;         // leaves of 2 .. leaf-1 keys
+  uint32_t* leaves_part_count;
+  uint32_t* work_counter;    // dynamic scheduling counter (zeroed per launch)
+  int* error;                // first error code
+  uint32_t leaf;
+  uint64_t lower, upper;     // strategy units
+};
+
+int launch_split_level(const SearchArgs& a, uint64_t max_m, uint64_t max_nodes, int sm_count, cudaStream_t s);
+int launch_leaves(const SearchArgs& a, uint64_t max_nodes, int sm_count, cudaStream_t s);
+
+}  // namespace rs

@@ -1,0 +1,119 @@
+// Lookup (Sec. 4, Sec. 6.2): signature -> bucket -> s_b, s_{b+1}, o_b from
+// the double Elias-Fano lists (Sec. 6.3, Sec. 7.4) -> descent of the bucket's
+// splitting tree.  At every split the key's part j is computed with the
+// node's stored index; moving to child j skips the j earlier siblings, whose
+// fixed parts are skipped with the table (a pointer move) and whose unary
+// parts are skipped by counting j * codes(unit) ones; at the leaf the
+// bijection's value is added to the keys left behind (c) and to s_b.
+#include "device.cuh"
+
+namespace rs {
+namespace {
+
+__device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint64_t lo) {
+  if (v.nb == 0) return 0;
+  const uint64_t b = bucket_of(hi, v.nb);
+  const uint32_t rec_w = v.low_a + v.low_b;
+  const uint64_t rec = b * rec_w;
+  const uint64_t pa = ef_select(v, 0, b);
+  const uint64_t pa1 = next_one(v.upper_a, pa + 1);
+  const uint64_t xa0 = ((pa - b) << v.low_a) | read_bits(v.lower, rec, v.low_a);
+  const uint64_t xa1 = ((pa1 - b - 1) << v.low_a) | read_bits(v.lower, rec + rec_w, v.low_a);
+  const uint64_t s0 = xa0 + static_cast<uint64_t>(static_cast<int64_t>(b) * v.delta_a);
+  const uint64_t s1 = xa1 + static_cast<uint64_t>(static_cast<int64_t>(b + 1) * v.delta_a);
+  uint32_t m = static_cast<uint32_t>(s1 - s0);
+  if (m <= 1) return s0;
+  const uint64_t pb = ef_select(v, 1, b);
+  const uint64_t xb = ((pb - b) << v.low_b) | read_bits(v.lower, rec + v.low_a, v.low_b);
+  const int64_t z = static_cast<int64_t>(xb) + static_cast<int64_t>(b) * v.delta_b;
+  const uint64_t bs = (__umul64hi(s0, v.beta) << 32) | ((s0 * v.beta) >> 32);
+  const uint64_t o = static_cast<uint64_t>(z + static_cast<int64_t>(bs));
+
+  uint64_t fixed = o;
+  uint64_t unary = o + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
+  uint64_t c = 0;
+  const uint64_t xpre = pre_key(lo);
+  for (uint32_t depth = 0;; depth++) {
+    const uint64_t w1 = __ldg(v.table + kTableWords * m + 1);
+    const uint32_t r = static_cast<uint32_t>(w1 >> 40) & 31;
+    const uint32_t fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
+    const uint32_t unit = static_cast<uint32_t>(w1);
+    const uint64_t low = read_bits(v.tree, fixed, r);
+    fixed += r;
+    const uint64_t one = next_one(v.tree, unary);
+    const uint64_t seed = ((one - unary) << r) | low;
+    unary = one + 1;
+    const uint32_t val = phi_pre(xpre, family_key(seed, depth), m);
+    if (fanout == 0) return s0 + c + val;
+    const uint32_t part = min(val / unit, fanout - 1);
+    if (part) {
+      const uint64_t wu = __ldg(v.table + kTableWords * unit);
+      fixed += uint64_t(part) * static_cast<uint32_t>(wu);
+      const uint64_t skip = uint64_t(part) * (wu >> 32);
+      if (skip) unary = select_from(v.tree, unary, skip - 1) + 1;
+      c += uint64_t(part) * unit;
+    }
+    m = part + 1 < fanout ? unit : m - unit * (fanout - 1);
+    if (m <= 1) return s0 + c;
+  }
+}
+
+__global__ void k_lookup_u64(View v, const uint64_t* __restrict__ keys, uint64_t q, uint64_t* __restrict__ out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t hi, lo;
+    signature_u64(__ldg(keys + i), hi, lo);
+    out[i] = lookup_one(v, hi, lo);
+  }
+}
+
+__global__ void k_lookup_bytes(View v, const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ offsets,
+                               uint64_t q, uint64_t* __restrict__ out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
+    uint64_t hi, lo;
+    signature_bytes(bytes + o0, o1 - o0, hi, lo);
+    out[i] = lookup_one(v, hi, lo);
+  }
+}
+
+}  // namespace
+
+View make_view(const Handle& h) {
+  View v;
+  const uint64_t* H = h.header;
+  v.tree = h.d_blob + h.layout.tree;
+  v.lower = h.d_blob + h.layout.lower;
+  v.upper_a = h.d_blob + h.layout.upper_a;
+  v.upper_b = h.d_blob + h.layout.upper_b;
+  v.anchors = h.d_blob + h.layout.anchors;
+  v.subs = reinterpret_cast<const uint16_t*>(h.d_blob + h.layout.subs);
+  v.table = h.d_table;
+  v.nb = H[H_NB];
+  v.beta = H[H_BETA];
+  v.delta_a = static_cast<int64_t>(H[H_DELTA_A]);
+  v.delta_b = static_cast<int64_t>(H[H_DELTA_B]);
+  v.low_a = static_cast<uint32_t>(H[H_LOW_A]);
+  v.low_b = static_cast<uint32_t>(H[H_LOW_B]);
+  v.leaf = static_cast<uint32_t>(H[H_LEAF]);
+  return v;
+}
+
+int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s) {
+  if (q.n == 0) return RECSPLIT_OK;
+  const View v = make_view(h);
+  int dev = 0, sms = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int block = 256;
+  const uint64_t want = (q.n + block - 1) / block;
+  const unsigned grid = static_cast<unsigned>(want < uint64_t(sms) * 64 ? want : uint64_t(sms) * 64);
+  if (q.u64)
+    k_lookup_u64<<<grid, block, 0, s>>>(v, q.u64, q.n, d_out);
+  else
+    k_lookup_bytes<<<grid, block, 0, s>>>(v, q.bytes, q.offsets, q.n, d_out);
+  count_launch();
+  RS_CUDA(cudaGetLastError());
+  return RECSPLIT_OK;
+}
+
+}  // namespace rs

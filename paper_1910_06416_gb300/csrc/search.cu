@@ -1,0 +1,430 @@
+// Brute-force searches of Sec. 4: for every split node the first function
+// index whose values send exactly k_t keys into the t-th interval of [0, m)
+// (Sec. 5.1), and for every leaf the first index that maps the leaf's keys
+// onto [0, m) (Sec. 5.2).
+//
+// Work unit: one node, searched by a group of G warps (G = 1, 2, 4 or 8 of the
+// 8 warps of a CTA).  Lane L of warp w of a group tests indices
+// w*32 + L, w*32 + L + 32G, ...; a warp stops after the round in which one of
+// its lanes succeeds, or as soon as the group's best success so far is below
+// its next round.  Every index below the final minimum has then been tested
+// by its owner, so the group minimum is the first successful index (the
+// result is deterministic and independent of G).  Nodes are handed out by an
+// atomic counter (persistent CTAs), the heaviest levels with larger groups.
+#include <algorithm>
+
+#include "device.cuh"
+
+namespace rs {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ void group_sync(uint32_t gid, uint32_t gwarps) {
+  if (gwarps == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(gwarps * 32) : "memory");
+  }
+}
+
+__device__ __forceinline__ uint64_t shl64(uint64_t x, uint32_t s) {
+  uint64_t r;  // PTX clamps shift amounts above 64 to 64 (result 0)
+  asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+}
+__device__ __forceinline__ uint32_t shl32(uint32_t x, uint32_t s) {
+  uint32_t r;  // clamps above 32 (result 0)
+  asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
+  return r;
+}
+
+__device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ uint64_t volatile_load(const uint64_t* p) {
+  return *reinterpret_cast<const volatile uint64_t*>(p);
+}
+
+// Stall threshold: a node that has not succeeded after 64 times its expected
+// number of trials (probability about e^-64) is checked for keys that can
+// never be separated.
+__device__ __forceinline__ uint64_t stall_threshold(const uint64_t* table, uint32_t m) {
+  const uint64_t e = table[kTableWords * m + 2];
+  return e > (kMaxTrials >> 6) ? kMaxTrials : e << 6;
+}
+
+// Trial limit of a node: 2^36, or 1024 times its expected number of trials
+// (at least 4096) if that is smaller.  A correct search passes it with
+// probability below e^-1024; the limit bounds the time of a search that can
+// never succeed.
+__device__ __forceinline__ uint64_t trial_limit(const uint64_t* table, uint32_t m) {
+  const uint64_t e = table[kTableWords * m + 2];
+  if (e > (kMaxTrials >> 10)) return kMaxTrials;
+  return max(uint64_t(4096), e << 10);
+}
+
+// ---------------------------------------------------------------- split trial
+// Part t of a key is floor(phi / unit) (at most fanout - 1).  Counts of the
+// first fanout - 1 parts are packed in fields of B bits (2^B > m, so no field
+// overflows); success iff the packed sum equals the packed target.
+struct SplitParams {
+  uint32_t m, unit, fanout, bits, magic;  // magic = ceil(2^32 / unit), exact for m < 2^16
+  uint64_t target, mask;
+};
+
+template <int MODE>  // 0: 32-bit fields + magic, 1: 64-bit fields + magic, 2: 64-bit + division
+__device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, const SplitParams& p,
+                                            uint64_t kp) {
+  if (MODE == 0) {
+    uint32_t acc = 0;
+#pragma unroll 4
+    for (uint32_t j = 0; j < p.m; j++) {
+      const uint32_t v = phi_pre(keys[j], kp, p.m);
+      acc += shl32(1u, __umulhi(v, p.magic) * p.bits);
+    }
+    return (acc & static_cast<uint32_t>(p.mask)) == static_cast<uint32_t>(p.target);
+  } else {
+    uint64_t acc = 0;
+#pragma unroll 4
+    for (uint32_t j = 0; j < p.m; j++) {
+      const uint32_t v = phi_pre(keys[j], kp, p.m);
+      const uint32_t part = MODE == 1 ? __umulhi(v, p.magic) : min(v / p.unit, p.fanout - 1);
+      acc += shl64(1ull, part * p.bits);
+    }
+    return (acc & p.mask) == p.target;
+  }
+}
+
+// Any two equal keys (they can never be separated)?  Lanes split the pairs.
+__device__ bool has_duplicate(const uint64_t* keys, uint32_t m, uint32_t lane) {
+  bool dup = false;
+  for (uint32_t i = lane; i < m && !dup; i += 32) {
+    const uint64_t x = keys[i];
+    for (uint32_t j = i + 1; j < m; j++)
+      if (keys[j] == x) {
+        dup = true;
+        break;
+      }
+  }
+  return __any_sync(0xFFFFFFFFu, dup);
+}
+
+template <int MODE>
+__device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ keys, const SplitParams& sp,
+                                                  uint32_t depth, uint32_t wig, uint32_t gwarps, uint32_t lane,
+                                                  uint64_t* best, uint64_t stall, uint64_t limit,
+                                                  int* err) {
+  bool checked = false;
+  for (uint64_t base = uint64_t(wig) * 32;; base += uint64_t(gwarps) * 32) {
+    if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(best))) break;
+    if (base >= limit) {
+      if (lane == 0) {
+        set_error(err, RECSPLIT_E_SEARCH_LIMIT);
+        atomicMin(reinterpret_cast<unsigned long long*>(best), 0ull);
+      }
+      break;
+    }
+    if (!checked && base >= stall) {
+      checked = true;
+      if (has_duplicate(keys, sp.m, lane)) {
+        if (lane == 0) {
+          set_error(err, RECSPLIT_E_DUPLICATE);
+          atomicMin(reinterpret_cast<unsigned long long*>(best), 0ull);
+        }
+        break;
+      }
+    }
+    const uint64_t kp = family_key(base + lane, depth);
+    const bool ok = split_trial<MODE>(keys, sp, kp);
+    const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+    if (hits) {
+      if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(best), base + __ffs(hits) - 1);
+      break;
+    }
+  }
+}
+
+__device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, const SplitParams& sp, int mode,
+                                             uint32_t depth, uint32_t wig, uint32_t gwarps, uint32_t lane,
+                                             uint64_t* best, uint64_t stall, uint64_t limit, int* err) {
+  if (mode == 0)
+    split_search_warp<0>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err);
+  else if (mode == 1)
+    split_search_warp<1>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err);
+  else
+    split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err);
+}
+
+// Emits the children of a split node with at least two keys into the queues
+// of full leaves, partial leaves or next-level splits (one warp).
+__device__ void emit_children(const SearchArgs& a, const Node& nd, uint32_t unit, uint32_t fanout,
+                              uint32_t lane) {
+  const uint32_t t = lane;
+  const uint32_t k = t + 1 < fanout ? unit : nd.m - unit * (fanout - 1);
+  const bool valid = t < fanout && k >= 2;
+  const uint32_t cls = k == a.leaf ? 0 : (k < a.leaf ? 1 : 2);
+  const uint32_t unit_codes = static_cast<uint32_t>(a.table[kTableWords * unit] >> 32);
+  Node child;
+  child.start = nd.start + t * unit;
+  child.m = k;
+  child.slot = nd.slot + 1 + t * unit_codes;
+  child.depth = nd.depth + 1;
+#pragma unroll
+  for (uint32_t c = 0; c < 3; c++) {
+    const bool mine = valid && cls == c;
+    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, mine);
+    if (!ballot) continue;
+    const uint32_t leader = __ffs(ballot) - 1;
+    Node* q = c == 0 ? a.leaves_full : (c == 1 ? a.leaves_part : a.split_out);
+    uint32_t* cnt = c == 0 ? a.leaves_full_count : (c == 1 ? a.leaves_part_count : a.split_out_count);
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(ballot));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (mine) q[base + __popc(ballot & ((1u << lane) - 1))] = child;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_split_level(SearchArgs a, uint32_t gwarps, uint32_t cap) {
+  extern __shared__ uint64_t staged[];
+  __shared__ uint64_t best[kWarps];
+  __shared__ uint32_t task[kWarps];
+  __shared__ uint32_t fill[kWarps][16];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t gid = warp / gwarps, wig = warp % gwarps;
+  const uint32_t tig = wig * 32 + lane, gthreads = gwarps * 32;
+  const bool leader = wig == 0 && lane == 0;
+  const uint32_t total = *a.split_in_count;
+  uint64_t* mine = staged + size_t(gid) * cap;
+
+  for (;;) {
+    if (leader) task[gid] = *reinterpret_cast<volatile int*>(a.error) ? total : atomicAdd(a.work_counter, 1u);
+    group_sync(gid, gwarps);
+    const uint32_t idx = task[gid];
+    if (idx >= total) break;
+    const Node nd = a.split_in[idx];
+    const uint64_t w1 = a.table[kTableWords * nd.m + 1];
+    SplitParams sp;
+    sp.m = nd.m;
+    sp.unit = static_cast<uint32_t>(w1);
+    sp.fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
+    sp.bits = 32 - __clz(nd.m);
+    sp.magic = static_cast<uint32_t>((0x100000000ull + sp.unit - 1) / sp.unit);
+    const uint32_t fields = sp.fanout - 1;
+    sp.target = 0;
+    for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
+    sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
+    const int mode = nd.m >= 65536 ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+    const uint64_t stall = stall_threshold(a.table, nd.m);
+    const uint64_t limit = trial_limit(a.table, nd.m);
+
+    const uint64_t* src = a.keys[nd.depth & 1] + nd.start;
+    uint64_t* dst = a.keys[(nd.depth + 1) & 1] + nd.start;
+    const bool in_smem = nd.m <= cap;
+    if (in_smem)
+      for (uint32_t j = tig; j < nd.m; j += gthreads) mine[j] = src[j];
+    if (leader) best[gid] = ~0ull;
+    if (tig < 16) fill[gid][tig] = 0;
+    group_sync(gid, gwarps);
+
+    if (in_smem)
+      split_search(mine, sp, mode, nd.depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+    else
+      split_search(src, sp, mode, nd.depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+    group_sync(gid, gwarps);
+
+    const uint64_t seed = best[gid];
+    if (!*reinterpret_cast<volatile int*>(a.error)) {
+      if (leader) {
+        a.seeds[nd.slot] = seed;
+        a.sizes[nd.slot] = nd.m;
+      }
+      // partition the keys into the children's ranges of the other array
+      const uint64_t kp = family_key(seed, nd.depth);
+      const uint64_t* from = in_smem ? mine : src;
+      for (uint32_t j = tig; j < nd.m; j += gthreads) {
+        const uint64_t x = from[j];
+        const uint32_t v = phi_pre(x, kp, nd.m);
+        const uint32_t part = min(v / sp.unit, sp.fanout - 1);
+        const uint32_t pos = atomicAdd(&fill[gid][part], 1u);
+        const uint32_t at = part * sp.unit + pos;
+        if (at < nd.m)
+          dst[at] = x;
+        else
+          set_error(a.error, RECSPLIT_E_INVALID);  // unreachable for a correct split
+      }
+      if (wig == 0) emit_children(a, nd, sp.unit, sp.fanout, lane);
+    }
+    group_sync(gid, gwarps);
+  }
+}
+
+// ---------------------------------------------------------------- leaves
+// Leaf of exactly L keys (the common case): keys in registers, bijection
+// test as an OR of one-hot bits compared with 2^L - 1.
+template <int L>
+__device__ __forceinline__ bool leaf_trial_full(const uint64_t (&x)[L], uint64_t kp) {
+  uint32_t seen = 0;
+#pragma unroll
+  for (int j = 0; j < L; j++) seen |= 1u << phi_pre(x[j], kp, L);
+  return seen == (L == 32 ? ~0u : ((1u << L) - 1));
+}
+
+// Leaf of m < LMAX keys: slots j >= m contribute nothing.
+template <int LMAX>
+__device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const uint32_t (&keep)[LMAX], uint32_t m,
+                                                uint64_t kp) {
+  uint32_t seen = 0;
+#pragma unroll
+  for (int j = 0; j < LMAX; j++) seen |= (1u << phi_pre(x[j], kp, m)) & keep[j];
+  return seen == (1u << m) - 1;
+}
+
+template <int LMAX, bool FULL>
+__global__ void __launch_bounds__(kThreads) k_leaves(SearchArgs a, uint32_t gwarps, uint32_t chunk) {
+  __shared__ uint64_t best[kWarps];
+  __shared__ uint32_t task[kWarps];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t gid = warp / gwarps, wig = warp % gwarps;
+  const bool leader = wig == 0 && lane == 0;
+  const Node* queue = FULL ? a.leaves_full : a.leaves_part;
+  const uint32_t total = FULL ? *a.leaves_full_count : *a.leaves_part_count;
+
+  for (;;) {
+    if (leader) task[gid] = *reinterpret_cast<volatile int*>(a.error) ? total : atomicAdd(a.work_counter, chunk);
+    group_sync(gid, gwarps);
+    const uint32_t first = task[gid];
+    if (first >= total) break;
+    const uint32_t last = min(total, first + chunk);
+    for (uint32_t idx = first; idx < last; idx++) {
+      const Node nd = queue[idx];
+      const uint32_t m = FULL ? LMAX : nd.m;
+      const uint64_t* src = a.keys[nd.depth & 1] + nd.start;
+      uint64_t x[LMAX];
+      uint32_t keep[LMAX];
+#pragma unroll
+      for (int j = 0; j < LMAX; j++) {
+        x[j] = (FULL || uint32_t(j) < m) ? __ldg(src + j) : 0;
+        keep[j] = (FULL || uint32_t(j) < m) ? ~0u : 0u;
+      }
+      if (leader) best[gid] = ~0ull;
+      group_sync(gid, gwarps);
+      const uint64_t stall = stall_threshold(a.table, m);
+      const uint64_t limit = trial_limit(a.table, m);
+      bool checked = false;
+      for (uint64_t base = uint64_t(wig) * 32;; base += uint64_t(gwarps) * 32) {
+        if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(&best[gid]))) break;
+        if (base >= limit) {
+          if (lane == 0) {
+            set_error(a.error, RECSPLIT_E_SEARCH_LIMIT);
+            atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), 0ull);
+          }
+          break;
+        }
+        if (!checked && base >= stall) {
+          checked = true;
+          bool dup = false;
+#pragma unroll
+          for (int i = 0; i < LMAX; i++)
+#pragma unroll
+            for (int j = i + 1; j < LMAX; j++) dup |= keep[j] && x[i] == x[j];
+          if (dup) {
+            if (lane == 0) {
+              set_error(a.error, RECSPLIT_E_DUPLICATE);
+              atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), 0ull);
+            }
+            break;
+          }
+        }
+        const uint64_t kp = family_key(base + lane, nd.depth);
+        const bool ok = FULL ? leaf_trial_full<LMAX>(x, kp) : leaf_trial_part<LMAX>(x, keep, m, kp);
+        const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+        if (hits) {
+          if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), base + __ffs(hits) - 1);
+          break;
+        }
+      }
+      group_sync(gid, gwarps);
+      if (leader) {
+        a.seeds[nd.slot] = best[gid];
+        a.sizes[nd.slot] = m;
+      }
+      group_sync(gid, gwarps);
+    }
+  }
+}
+
+template <typename K>
+int persistent_grid(K kernel, size_t smem, int sm_count, int* blocks) {
+  int per_sm = 0;
+  RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+  if (per_sm < 1) return fail(RECSPLIT_E_INVALID, "search kernel does not fit on an SM");
+  *blocks = per_sm * sm_count;
+  return RECSPLIT_OK;
+}
+
+template <int LMAX, bool FULL>
+int launch_leaf_kernel(const SearchArgs& a, uint32_t gwarps, uint32_t chunk, int sm_count, cudaStream_t s) {
+  auto kern = k_leaves<LMAX, FULL>;
+  int blocks = 0;
+  int rc = persistent_grid(kern, 0, sm_count, &blocks);
+  if (rc) return rc;
+  RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
+  kern<<<blocks, kThreads, 0, s>>>(a, gwarps, chunk);
+  count_launch();
+  RS_CUDA(cudaGetLastError());
+  return RECSPLIT_OK;
+}
+
+template <int L>
+int launch_full(const SearchArgs& a, uint32_t gw, uint32_t chunk, int sm, cudaStream_t s) {
+  return launch_leaf_kernel<L, true>(a, gw, chunk, sm, s);
+}
+
+typedef int (*FullLauncher)(const SearchArgs&, uint32_t, uint32_t, int, cudaStream_t);
+constexpr FullLauncher kFull[25] = {
+    nullptr,         nullptr,         launch_full<2>,  launch_full<3>,  launch_full<4>,
+    launch_full<5>,  launch_full<6>,  launch_full<7>,  launch_full<8>,  launch_full<9>,
+    launch_full<10>, launch_full<11>, launch_full<12>, launch_full<13>, launch_full<14>,
+    launch_full<15>, launch_full<16>, launch_full<17>, launch_full<18>, launch_full<19>,
+    launch_full<20>, launch_full<21>, launch_full<22>, launch_full<23>, launch_full<24>};
+
+}  // namespace
+
+int launch_split_level(const SearchArgs& a, uint64_t max_m, uint64_t max_nodes, int sm_count, cudaStream_t s) {
+  (void)max_nodes;
+  // heavier nodes get more warps: fewer nodes per level and longer searches
+  uint32_t gwarps = 1;
+  if (max_m >= 256)
+    gwarps = 8;
+  else if (max_m >= 64 && a.leaf >= 12)
+    gwarps = 2;
+  const uint32_t groups = kWarps / gwarps;
+  const size_t budget = 96 * 1024;
+  uint64_t cap = std::min<uint64_t>(max_m, budget / (groups * sizeof(uint64_t)));
+  if (cap < 1) cap = 1;
+  const size_t smem = size_t(groups) * cap * sizeof(uint64_t);
+  RS_CUDA(cudaFuncSetAttribute(k_split_level, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int blocks = 0;
+  int rc = persistent_grid(k_split_level, smem, sm_count, &blocks);
+  if (rc) return rc;
+  RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
+  k_split_level<<<blocks, kThreads, smem, s>>>(a, gwarps, static_cast<uint32_t>(cap));
+  count_launch();
+  RS_CUDA(cudaGetLastError());
+  return RECSPLIT_OK;
+}
+
+int launch_leaves(const SearchArgs& a, uint64_t max_nodes, int sm_count, cudaStream_t s) {
+  (void)max_nodes;
+  if (a.leaf < 2) return RECSPLIT_OK;
+  const uint32_t gwarps = a.leaf >= 12 ? 4 : 1;
+  const uint32_t chunk = a.leaf >= 12 ? 1 : 4;
+  int rc = kFull[a.leaf](a, gwarps, chunk, sm_count, s);
+  if (rc) return rc;
+  if (a.leaf <= 8) return launch_leaf_kernel<8, false>(a, gwarps, chunk, sm_count, s);
+  if (a.leaf <= 16) return launch_leaf_kernel<16, false>(a, gwarps, chunk, sm_count, s);
+  return launch_leaf_kernel<24, false>(a, gwarps, chunk, sm_count, s);
+}
+
+}  // namespace rs

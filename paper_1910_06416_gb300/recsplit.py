@@ -1,0 +1,263 @@
+"""Thin ctypes binding of the C ABI in ``include/recsplit.h``.
+
+The functions carry the C names and only marshal arguments: every step of
+construction and lookup runs in the CUDA library.  Arrays may be torch
+tensors (CUDA or CPU) or numpy arrays; their data pointers are passed as
+they are and the library copies host buffers itself.  Loading fails loudly
+if the compiled library is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "librecsplit.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "recsplit.h")
+
+OK = 0
+E_INVALID, E_DUPLICATE, E_SEARCH_LIMIT, E_NOMEM, E_CUDA = -1, -2, -4, -5, -6
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("leaf_size", C.c_uint32), ("bucket_size", C.c_uint32),
+                ("num_buckets", C.c_uint64), ("tree_bits", C.c_uint64), ("total_bits", C.c_uint64),
+                ("max_bucket", C.c_uint64), ("num_codes", C.c_uint64), ("tree_bits_per_key", C.c_double),
+                ("bits_per_key", C.c_double)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms_signature", C.c_double), ("ms_group", C.c_double), ("ms_split", C.c_double),
+                ("ms_leaf", C.c_double), ("ms_encode", C.c_double), ("ms_total", C.c_double),
+                ("split_nodes", C.c_uint64), ("split_trials", C.c_uint64), ("split_evals", C.c_uint64),
+                ("leaf_nodes", C.c_uint64), ("leaf_trials", C.c_uint64), ("leaf_evals", C.c_uint64),
+                ("launches", C.c_uint32), ("split_levels", C.c_uint32)]
+
+
+class RecSplitError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = _lib
+        msg = lib.recsplit_strerror(code).decode() if lib else str(code)
+        detail = lib.recsplit_last_error().decode() if lib else ""
+        super().__init__(f"{where}: {msg} ({code}){': ' + detail if detail else ''}")
+        self.code = code
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise OSError(f"{LIB_PATH} is missing: build it with `python -m paper_1910_06416_gb300.build`")
+            L = C.CDLL(LIB_PATH)
+            p, u64, u32, i = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int
+            L.recsplit_build_u64.argtypes = [p, u64, u32, u32, p, C.POINTER(p)]
+            L.recsplit_build.argtypes = [p, u64, u32, u32, p, C.POINTER(p)]
+            L.recsplit_build_bytes.argtypes = [p, p, u64, u32, u32, p, C.POINTER(p)]
+            L.recsplit_lookup_u64.argtypes = [p, p, u64, p, p]
+            L.recsplit_lookup.argtypes = [p, p, u64, p, p]
+            L.recsplit_lookup_bytes.argtypes = [p, p, p, u64, p, p]
+            L.recsplit_serialize.argtypes = [p, p, C.c_size_t, C.POINTER(C.c_size_t)]
+            L.recsplit_deserialize.argtypes = [p, C.c_size_t, p, C.POINTER(p)]
+            L.recsplit_stats.argtypes = [p, C.POINTER(Stats)]
+            L.recsplit_free.argtypes = [p]
+            L.recsplit_free.restype = None
+            L.recsplit_strerror.argtypes = [i]
+            L.recsplit_strerror.restype = C.c_char_p
+            L.recsplit_last_error.argtypes = []
+            L.recsplit_last_error.restype = C.c_char_p
+            L.recsplit_golomb_rice_params.argtypes = [u32, u64, p]
+            L.recsplit_set_profiling.argtypes = [i]
+            L.recsplit_last_profile.argtypes = [C.POINTER(Profile)]
+            L.recsplit_launch_count.argtypes = []
+            L.recsplit_launch_count.restype = u64
+            for name in ("recsplit_build_u64", "recsplit_build", "recsplit_build_bytes", "recsplit_lookup_u64",
+                         "recsplit_lookup", "recsplit_lookup_bytes", "recsplit_serialize", "recsplit_deserialize",
+                         "recsplit_stats", "recsplit_golomb_rice_params", "recsplit_set_profiling",
+                         "recsplit_last_profile"):
+                getattr(L, name).restype = i
+            _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/recsplit.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(recsplit_[a-z0-9_]+)\s*\(", text)))
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise RecSplitError(rc, where)
+
+
+def _count(x) -> int:
+    return int(x.shape[0])
+
+
+# ---------------------------------------------------------------- C names
+def recsplit_build_u64(keys, leaf_size: int, bucket_size: int, stream=None) -> int:
+    """Build from 64-bit keys; returns the opaque handle (an int)."""
+    h = C.c_void_p()
+    _check(lib().recsplit_build_u64(_ptr(keys), _count(keys), leaf_size, bucket_size, _stream(stream), C.byref(h)),
+           "recsplit_build_u64")
+    return h.value
+
+
+def recsplit_build(keys, leaf_size: int, bucket_size: int, stream=None) -> int:
+    h = C.c_void_p()
+    _check(lib().recsplit_build(_ptr(keys), _count(keys), leaf_size, bucket_size, _stream(stream), C.byref(h)),
+           "recsplit_build")
+    return h.value
+
+
+def recsplit_build_bytes(data, offsets, leaf_size: int, bucket_size: int, stream=None) -> int:
+    h = C.c_void_p()
+    _check(lib().recsplit_build_bytes(_ptr(data), _ptr(offsets), _count(offsets) - 1, leaf_size, bucket_size,
+                                      _stream(stream), C.byref(h)), "recsplit_build_bytes")
+    return h.value
+
+
+def recsplit_lookup_u64(h: int, keys, out, stream=None) -> None:
+    _check(lib().recsplit_lookup_u64(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
+           "recsplit_lookup_u64")
+
+
+def recsplit_lookup(h: int, keys, out, stream=None) -> None:
+    _check(lib().recsplit_lookup(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
+           "recsplit_lookup")
+
+
+def recsplit_lookup_bytes(h: int, data, offsets, out, stream=None) -> None:
+    _check(lib().recsplit_lookup_bytes(C.c_void_p(h), _ptr(data), _ptr(offsets), _count(offsets) - 1, _ptr(out),
+                                       _stream(stream)), "recsplit_lookup_bytes")
+
+
+def recsplit_serialize(h: int) -> np.ndarray:
+    """The serialized structure as uint64 words."""
+    n = C.c_size_t()
+    _check(lib().recsplit_serialize(C.c_void_p(h), None, 0, C.byref(n)), "recsplit_serialize")
+    buf = np.zeros(n.value // 8, dtype=np.uint64)
+    _check(lib().recsplit_serialize(C.c_void_p(h), _ptr(buf), n.value, C.byref(n)), "recsplit_serialize")
+    return buf
+
+
+def recsplit_deserialize(words: np.ndarray, stream=None) -> int:
+    words = np.ascontiguousarray(words, dtype=np.uint64)
+    h = C.c_void_p()
+    _check(lib().recsplit_deserialize(_ptr(words), words.nbytes, _stream(stream), C.byref(h)),
+           "recsplit_deserialize")
+    return h.value
+
+
+def recsplit_stats(h: int) -> dict:
+    st = Stats()
+    _check(lib().recsplit_stats(C.c_void_p(h), C.byref(st)), "recsplit_stats")
+    return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def recsplit_free(h: int) -> None:
+    if h:
+        lib().recsplit_free(C.c_void_p(h))
+
+
+def recsplit_strerror(code: int) -> str:
+    return lib().recsplit_strerror(code).decode()
+
+
+def recsplit_last_error() -> str:
+    return lib().recsplit_last_error().decode()
+
+
+def recsplit_golomb_rice_params(leaf_size: int, m_hi: int) -> np.ndarray:
+    out = np.zeros(m_hi + 1, dtype=np.uint8)
+    _check(lib().recsplit_golomb_rice_params(leaf_size, m_hi, _ptr(out)), "recsplit_golomb_rice_params")
+    return out
+
+
+def recsplit_set_profiling(enabled: bool) -> None:
+    _check(lib().recsplit_set_profiling(1 if enabled else 0), "recsplit_set_profiling")
+
+
+def recsplit_last_profile() -> dict:
+    pr = Profile()
+    _check(lib().recsplit_last_profile(C.byref(pr)), "recsplit_last_profile")
+    return {name: getattr(pr, name) for name, _ in Profile._fields_}
+
+
+def recsplit_launch_count() -> int:
+    return int(lib().recsplit_launch_count())
+
+
+# ---------------------------------------------------------------- convenience
+class Structure:
+    """Owning wrapper of a handle (frees it when collected)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @classmethod
+    def build_u64(cls, keys, leaf_size: int, bucket_size: int, stream=None) -> "Structure":
+        return cls(recsplit_build_u64(keys, leaf_size, bucket_size, stream))
+
+    @classmethod
+    def build_bytes(cls, data, offsets, leaf_size: int, bucket_size: int, stream=None) -> "Structure":
+        return cls(recsplit_build_bytes(data, offsets, leaf_size, bucket_size, stream))
+
+    @classmethod
+    def deserialize(cls, words, stream=None) -> "Structure":
+        return cls(recsplit_deserialize(words, stream))
+
+    def lookup_u64(self, keys, out, stream=None):
+        recsplit_lookup_u64(self.handle, keys, out, stream)
+        return out
+
+    def lookup_bytes(self, data, offsets, out, stream=None):
+        recsplit_lookup_bytes(self.handle, data, offsets, out, stream)
+        return out
+
+    def serialize(self) -> np.ndarray:
+        return recsplit_serialize(self.handle)
+
+    def stats(self) -> dict:
+        return recsplit_stats(self.handle)
+
+    def free(self):
+        if self.handle:
+            recsplit_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

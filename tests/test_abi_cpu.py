@@ -1,0 +1,61 @@
+"""The C ABI library builds, loads and exports the declared symbols (no GPU)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def rs():
+    from paper_1910_06416_gb300 import build
+    build.build()
+    import paper_1910_06416_gb300.recsplit as rs
+    rs.lib()
+    return rs
+
+
+def test_library_exports_every_declared_function(rs):
+    names = rs.header_functions()
+    assert len(names) >= 13
+    raw = C.CDLL(rs.LIB_PATH)
+    for name in names:
+        assert hasattr(raw, name), name
+
+
+def test_binding_has_the_c_names(rs):
+    for name in rs.header_functions():
+        assert callable(getattr(rs, name)), name
+
+
+def test_error_strings(rs):
+    for code in (rs.OK, rs.E_INVALID, rs.E_DUPLICATE, rs.E_SEARCH_LIMIT, rs.E_NOMEM, rs.E_CUDA):
+        assert rs.recsplit_strerror(code)
+    assert rs.recsplit_strerror(-99) == "unknown error"
+
+
+def test_invalid_arguments_rejected_before_device_work(rs):
+    keys = np.arange(10, dtype=np.uint64)
+    for leaf, b in [(0, 5), (25, 5), (5, 0), (5, 65536)]:
+        with pytest.raises(rs.RecSplitError) as e:
+            rs.recsplit_build_u64(keys, leaf, b)
+        assert e.value.code == rs.E_INVALID
+    with pytest.raises(rs.RecSplitError):
+        rs.recsplit_deserialize(np.zeros(3, dtype=np.uint64))
+    bad = np.zeros(16, dtype=np.uint64)
+    bad[0] = 0x1234
+    with pytest.raises(rs.RecSplitError):
+        rs.recsplit_deserialize(bad)
+
+
+def test_golomb_rice_table_equals_oracle(rs, orc):
+    """The library derives its Golomb-Rice table independently of the oracle;
+    both must agree on every node size (Eq. gr below 2^16, Sec. 7.2 above)."""
+    for leaf in range(1, 25):
+        hi = 65535 if leaf in (1, 5, 8, 16, 24) else 4000
+        got = rs.recsplit_golomb_rice_params(leaf, hi)
+        want = np.array([orc.golomb_rice(leaf, m) for m in range(hi + 1)], dtype=np.uint8)
+        assert np.array_equal(got, want), leaf
+    for leaf in (5, 8, 16):
+        ms = [65536, 70000, 100000, 250001]
+        got = rs.recsplit_golomb_rice_params(leaf, max(ms))
+        assert [int(got[m]) for m in ms] == [orc.golomb_rice(leaf, m) for m in ms]
