@@ -69,7 +69,7 @@ __device__ __forceinline__ uint64_t trial_limit(const uint64_t* table, uint32_t 
 // first fanout - 1 parts are packed in fields of B bits (2^B > m, so no field
 // overflows); success iff the packed sum equals the packed target.
 struct SplitParams {
-  uint32_t m, unit, fanout, bits, magic;  // magic = ceil(2^32 / unit), exact for m < 2^16
+  uint32_t m, unit, fanout, bits, magic;  // magic = ceil(2^32 / unit): exact for m < 2^16, unit >= 2
   uint64_t target, mask;
 };
 
@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(kThreads) k_split_level(SearchArgs a, uint32_t
     sp.target = 0;
     for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
     sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
-    const int mode = nd.m >= 65536 ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+    // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
+    const int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
     const uint64_t stall = stall_threshold(a.table, nd.m);
     const uint64_t limit = trial_limit(a.table, nd.m);
 
