@@ -144,6 +144,25 @@ int recsplit_last_profile(recsplit_profile_t* out);
 /* Kernels launched by the library on the calling host thread so far. */
 uint64_t recsplit_launch_count(void);
 
+/* Largest number of keys one recsplit_lookup_u64_static call accepts. */
+#define RECSPLIT_STATIC_LOOKUP_MAX (1u << 20)
+
+/* Lookup of q <= RECSPLIT_STATIC_LOOKUP_MAX 64-bit keys that allocates no
+ * device memory (the paper has no counterpart: this is an interface for
+ * callers that cannot allocate while they serve lookups, e.g. a host thread in
+ * a process where another component's caching allocator has reserved all of
+ * the GPU's memory, or a request loop that must not take the allocator's locks
+ * and implicit synchronisation).  keys and out may be host or device memory;
+ * results equal recsplit_lookup_u64's.  Keys and results are staged through
+ * one fixed 16 MiB array in device memory that belongs to the library image
+ * (every GPU that loads the library holds it until the process exits).  The
+ * first call on a device looks up that array's device address, so make it
+ * before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (other host threads or streams) race and must be serialised by
+ * the caller.  q above the maximum fails with RECSPLIT_E_INVALID.  Returns
+ * after the results are in out. */
+int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
+
 /* Golomb-Rice parameters of nodes of 0 .. m_hi keys for leaf size l
  * (Sec. 5.4 Eq. gr with the probabilities of Sec. 5.1 / 5.2, and the integer
  * rule of Sec. 7.2 from 2^16 keys on): out[m] for m in [0, m_hi], host

@@ -77,12 +77,13 @@ def lib():
             L.recsplit_golomb_rice_params.argtypes = [u32, u64, p]
             L.recsplit_set_profiling.argtypes = [i]
             L.recsplit_last_profile.argtypes = [C.POINTER(Profile)]
+            L.recsplit_lookup_u64_static.argtypes = [p, p, u64, p, p]
             L.recsplit_launch_count.argtypes = []
             L.recsplit_launch_count.restype = u64
             for name in ("recsplit_build_u64", "recsplit_build", "recsplit_build_bytes", "recsplit_lookup_u64",
                          "recsplit_lookup", "recsplit_lookup_bytes", "recsplit_serialize", "recsplit_deserialize",
                          "recsplit_stats", "recsplit_golomb_rice_params", "recsplit_set_profiling",
-                         "recsplit_last_profile"):
+                         "recsplit_last_profile", "recsplit_lookup_u64_static"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -150,6 +151,15 @@ def recsplit_build_bytes(data, offsets, leaf_size: int, bucket_size: int, stream
 def recsplit_lookup_u64(h: int, keys, out, stream=None) -> None:
     _check(lib().recsplit_lookup_u64(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
            "recsplit_lookup_u64")
+
+
+STATIC_LOOKUP_MAX = 1 << 20
+
+
+def recsplit_lookup_u64_static(h: int, keys, out, stream=None) -> None:
+    """Lookup that allocates no device memory (at most STATIC_LOOKUP_MAX keys)."""
+    _check(lib().recsplit_lookup_u64_static(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
+           "recsplit_lookup_u64_static")
 
 
 def recsplit_lookup(h: int, keys, out, stream=None) -> None:
