@@ -97,12 +97,17 @@ uint64_t orc_bucket(uint64_t hi, uint64_t nbuckets) { return (uint64_t)(((u128)h
 /* Function number i at depth d is keyed by (i * 64 + d) times the Weyl
  * constant, so functions at different depths of one root-to-leaf path are
  * never the same.  It acts on the lower signature half only (the upper half
- * chose the bucket); the range reduction to [0, m) is fixed-point
- * multiplication of the top 32 bits, as the paper uses for buckets. */
+ * chose the bucket): the key is xored in and the first two xorshift-multiply
+ * rounds of the splitmix64 finalizer are applied (its last xorshift would only
+ * touch the lowest of the 32 bits kept).  The range reduction to [0, m) is
+ * fixed-point multiplication of the top 32 bits, as the paper uses for
+ * buckets. */
 uint32_t orc_phi(uint64_t lo, uint32_t depth, uint64_t index, uint64_t m) {
   uint64_t key = ((index << 6) | depth) * ORC_WEYL;
-  uint64_t h = orc_mix64(lo ^ key);
-  return (uint32_t)(((h >> 32) * m) >> 32);
+  uint64_t z = lo ^ key;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return (uint32_t)(((z >> 32) * m) >> 32);
 }
 
 /* ------------------------------------------------------------------ */

@@ -1,6 +1,7 @@
 // C ABI entry points (include/recsplit.h): argument checks, host/device
 // buffer staging, serialization and error reporting.
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "common.h"
@@ -20,6 +21,40 @@ int cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? RECSPLIT_E_NOMEM : RECSPLIT_E_CUDA;
+}
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+int device_pool(cudaMemPool_t* pool) {
+  int dev = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(RECSPLIT_E_INVALID, "device ordinal above 63");
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p;
+    RS_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = ~0ull;
+    RS_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = p;
+  }
+  *pool = g_pools[dev];
+  return RECSPLIT_OK;
+}
+
+int pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool;
+  int rc = device_pool(&pool);
+  if (rc) return rc;
+  if (cudaMallocFromPoolAsync(p, bytes ? bytes : 8, pool, s) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RECSPLIT_E_NOMEM, "device allocation failed");
+  }
+  return RECSPLIT_OK;
 }
 
 static thread_local bool g_profiling = false;
@@ -61,10 +96,8 @@ struct Staged {
       dev = const_cast<void*>(p);
       return RECSPLIT_OK;
     }
-    if (cudaMallocAsync(&dev, bytes, s) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(RECSPLIT_E_NOMEM, "device allocation for staging host input failed");
-    }
+    int rc = pool_alloc(&dev, bytes, s);
+    if (rc) return rc;
     owned = true;
     RS_CUDA(cudaMemcpyAsync(dev, p, bytes, cudaMemcpyHostToDevice, s));
     return RECSPLIT_OK;
@@ -166,10 +199,7 @@ static int lookup_common(const recsplit_t* hp, const KeyInput& q_host_or_dev, bo
   uint64_t* d_out = out;
   if (!out_dev && q) {
     res.s = s;
-    if (cudaMallocAsync(&res.dev, q * sizeof(uint64_t), s) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(RECSPLIT_E_NOMEM, "device allocation for lookup results failed");
-    }
+    if ((rc = pool_alloc(&res.dev, q * sizeof(uint64_t), s))) return rc;
     res.owned = true;
     d_out = static_cast<uint64_t*>(res.dev);
   }

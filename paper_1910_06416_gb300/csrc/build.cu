@@ -312,11 +312,8 @@ struct Scratch {
   template <typename T>
   int alloc(T** p, uint64_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, std::max<uint64_t>(count, 1) * sizeof(T), s);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(RECSPLIT_E_NOMEM, "device allocation failed");
-    }
+    int rc = pool_alloc(&q, std::max<uint64_t>(count, 1) * sizeof(T), s);
+    if (rc) return rc;
     ptrs.push_back(q);
     *p = static_cast<T*>(q);
     return RECSPLIT_OK;

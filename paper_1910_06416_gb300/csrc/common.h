@@ -57,7 +57,8 @@ int golomb_rice_param(const Strategy& st, uint64_t m);
 // Per-size tables for node sizes 0 .. mmax.  Device form: four words per size
 //   w0 = fixed_bits(subtree) | codes(subtree) << 32
 //   w1 = unit | fanout << 32 | r << 40
-//   w2 = expected number of trials (1/p rounded up), w3 = 0
+//   w2 = expected number of trials (1/p rounded up)
+//   w3 = ceil(2^32 / unit) for unit >= 2 (exact floor(v / unit) for v < m < 2^16), else 0
 constexpr int kTableWords = 4;
 struct Tables {
   uint64_t mmax = 0;
@@ -95,6 +96,12 @@ struct View {
   uint32_t leaf;
 };
 View make_view(const Handle& h);
+
+// ---------------------------------------------------------------- memory
+// Stream-ordered pool of the current device that keeps freed memory for
+// reuse (no release at synchronisation points).
+int device_pool(cudaMemPool_t* pool);
+int pool_alloc(void** p, size_t bytes, cudaStream_t s);
 
 // ---------------------------------------------------------------- tracing
 bool profiling_enabled();

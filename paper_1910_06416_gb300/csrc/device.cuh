@@ -62,11 +62,12 @@ __device__ __forceinline__ void signature_bytes(const uint8_t* p, uint64_t len, 
 __device__ __forceinline__ uint64_t bucket_of(uint64_t hi, uint64_t nb) { return __umul64hi(hi, nb); }
 
 // ---------------------------------------------------------------- hash family
-// Function i at depth d acts on the lower half x as mix64(x ^ K) with
-// K = (i * 64 + d) * W (W the Weyl constant) and keeps the top 32 bits;
+// Function i at depth d acts on the lower half x: z = x ^ K with
+// K = (i * 64 + d) * W (W the Weyl constant), then the two xorshift-multiply
+// rounds of the splitmix64 finalizer, keeping the top 32 bits;
 // phi^m = floor(top32 * m / 2^32).  The searches keep, per key, the value
-// x ^ (x >> 30) and, per function, K ^ (K >> 30): the first xorshift of the
-// mixer distributes over the xor, so one mixer step is saved per evaluation.
+// x ^ (x >> 30) and, per function, K ^ (K >> 30): the first xorshift
+// distributes over the xor, so it costs nothing per evaluation.
 __host__ __device__ __forceinline__ uint64_t family_key(uint64_t index, uint32_t depth) {
   const uint64_t k = ((index << 6) | depth) * kWeyl;
   return k ^ (k >> 30);
@@ -74,15 +75,14 @@ __host__ __device__ __forceinline__ uint64_t family_key(uint64_t index, uint32_t
 
 __host__ __device__ __forceinline__ uint64_t pre_key(uint64_t x) { return x ^ (x >> 30); }
 
-// Top 32 bits of mix64(x ^ K) from the pre-shifted forms of x and K.
+// Top 32 bits of the family's hash from the pre-shifted forms of x and K.
 __device__ __forceinline__ uint32_t family_top32(uint64_t xpre, uint64_t kpre) {
   uint64_t z = (xpre ^ kpre) * kMixA;
   z ^= z >> 27;
   const uint32_t zl = static_cast<uint32_t>(z), zh = static_cast<uint32_t>(z >> 32);
   // high word of the low 64 bits of z * kMixB
-  const uint32_t t = __umulhi(zl, static_cast<uint32_t>(kMixB)) + zl * static_cast<uint32_t>(kMixB >> 32) +
-                     zh * static_cast<uint32_t>(kMixB);
-  return t ^ (t >> 31);
+  return __umulhi(zl, static_cast<uint32_t>(kMixB)) + zl * static_cast<uint32_t>(kMixB >> 32) +
+         zh * static_cast<uint32_t>(kMixB);
 }
 
 __device__ __forceinline__ uint32_t phi_pre(uint64_t xpre, uint64_t kpre, uint32_t m) {

@@ -45,7 +45,8 @@ __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint6
     unary = one + 1;
     const uint32_t val = phi_pre(xpre, family_key(seed, depth), m);
     if (fanout == 0) return s0 + c + val;
-    const uint32_t part = min(val / unit, fanout - 1);
+    const uint32_t magic = static_cast<uint32_t>(__ldg(v.table + kTableWords * m + 3));
+    const uint32_t part = min(magic && m < 65536 ? __umulhi(val, magic) : val / unit, fanout - 1);
     if (part) {
       const uint64_t wu = __ldg(v.table + kTableWords * unit);
       fixed += uint64_t(part) * static_cast<uint32_t>(wu);

@@ -84,7 +84,8 @@ int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t count, cudaSt
     return RECSPLIT_OK;
   }
   uint64_t* sums = nullptr;
-  RS_CUDA(cudaMallocAsync(&sums, (tiles + 1) * sizeof(uint64_t), s));
+  int rc0 = pool_alloc(reinterpret_cast<void**>(&sums), (tiles + 1) * sizeof(uint64_t), s);
+  if (rc0) return rc0;
   k_tile_sums<<<static_cast<unsigned>(tiles), kThreads, 0, s>>>(in, count, sums);
   count_launch();
   RS_CUDA(cudaGetLastError());

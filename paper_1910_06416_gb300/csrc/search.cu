@@ -185,7 +185,7 @@ __device__ void emit_children(const SearchArgs& a, const Node& nd, uint32_t unit
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_split_level(SearchArgs a, uint32_t gwarps, uint32_t cap) {
+__global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint32_t gwarps, uint32_t cap) {
   extern __shared__ uint64_t staged[];
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_split_level(SearchArgs a, uint32_t
       for (uint32_t j = tig; j < nd.m; j += gthreads) {
         const uint64_t x = from[j];
         const uint32_t v = phi_pre(x, kp, nd.m);
-        const uint32_t part = min(v / sp.unit, sp.fanout - 1);
+        const uint32_t part = min(mode == 2 ? v / sp.unit : __umulhi(v, sp.magic), sp.fanout - 1);
         const uint32_t pos = atomicAdd(&fill[gid][part], 1u);
         const uint32_t at = part * sp.unit + pos;
         if (at < nd.m)
@@ -281,8 +281,12 @@ __device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const
   return seen == (1u << m) - 1;
 }
 
+// Blocks per SM the register budget must allow (keys live in registers).
+constexpr int leaf_min_blocks(int l) { return l <= 5 ? 6 : (l <= 8 ? 5 : (l <= 16 ? 4 : 3)); }
+
 template <int LMAX, bool FULL>
-__global__ void __launch_bounds__(kThreads) k_leaves(SearchArgs a, uint32_t gwarps, uint32_t chunk) {
+__global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(SearchArgs a, uint32_t gwarps,
+                                                                            uint32_t chunk) {
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -113,6 +113,7 @@ int build_tables(uint32_t leaf, uint64_t mmax, Tables* T, std::string* err) {
     T->device_words[kTableWords * m + 1] =
         sh.unit | (static_cast<uint64_t>(sh.fanout) << 32) | (static_cast<uint64_t>(r) << 40);
     T->device_words[kTableWords * m + 2] = T->expected_trials[m];
+    T->device_words[kTableWords * m + 3] = sh.unit >= 2 ? ((1ull << 32) + sh.unit - 1) / sh.unit : 0;
   }
   // sizes 0 and 1: leaves without a code
   return RECSPLIT_OK;
