@@ -79,6 +79,33 @@ int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t
 int recsplit_build(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
                    recsplit_t** out);
 
+/* One key set of a batched build: 64-bit keys (keys != NULL) or byte strings
+ * (bytes and offsets with n + 1 entries), in device memory, with its own
+ * leaf size and bucket size. */
+typedef struct recsplit_keyset {
+  const uint64_t* keys;
+  const uint8_t* bytes;
+  const uint64_t* offsets;
+  uint64_t n;
+  uint32_t leaf_size;
+  uint32_t bucket_size;
+} recsplit_keyset_t;
+
+/* Builds count independent structures in one pass (Sec. 4 applied to every
+ * set; buckets of all sets are searched together, the search phase runs as
+ * one CUDA graph of persistent kernels).  outs[i] receives the structure of
+ * sets[i], identical to what recsplit_build_u64 / _bytes would build from it.
+ * All key arrays must be device memory; at most 2^32 - 1 keys in total and
+ * at most 25 distinct leaf sizes.  The structures share one device arena,
+ * released when the last of them is freed. */
+int recsplit_build_batch(const recsplit_keyset_t* sets, uint32_t count, void* stream, recsplit_t** outs);
+
+/* Batched lookup over several structures: out[i] = lookup of keys[i] in
+ * hs[ids[i]] (64-bit keys).  ids, keys and out: q entries each, device or
+ * host memory (all three of one kind). */
+int recsplit_lookup_batch(const recsplit_t* const* hs, uint32_t count, const uint32_t* ids, const uint64_t* keys,
+                          uint64_t q, uint64_t* out, void* stream);
+
 /* Lookup of q 64-bit keys (Sec. 4): out[i] = the index in [0, n) of keys[i]
  * for keys of the set; for other keys a deterministic value in [0, n]
  * (Sec. 1 allows any value).  keys and out: host or device. */

@@ -3,6 +3,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.h"
 
@@ -131,11 +132,13 @@ int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uin
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Staged k;
   if ((rc = k.from(keys, n * sizeof(uint64_t), n && on_device(keys), s))) return rc;
-  KeyInput in;
-  in.u64 = static_cast<const uint64_t*>(k.dev);
-  in.n = n;
+  SetInput in;
+  in.keys.u64 = static_cast<const uint64_t*>(k.dev);
+  in.keys.n = n;
+  in.leaf = leaf_size;
+  in.bucket_size = bucket_size;
   Handle* h = nullptr;
-  if ((rc = build_structure(in, leaf_size, bucket_size, s, &h))) return rc;
+  if ((rc = build_sets(&in, 1, BuildOptions{}, s, &h))) return rc;
   *out = reinterpret_cast<recsplit_t*>(h);
   return RECSPLIT_OK;
 }
@@ -164,13 +167,81 @@ int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t
     b.dev = const_cast<uint8_t*>(bytes);
     o.dev = const_cast<uint64_t*>(offsets);
   }
-  KeyInput in;
-  in.bytes = static_cast<const uint8_t*>(b.dev);
-  in.offsets = static_cast<const uint64_t*>(o.dev);
-  in.n = n;
+  SetInput in;
+  in.keys.bytes = static_cast<const uint8_t*>(b.dev);
+  in.keys.offsets = static_cast<const uint64_t*>(o.dev);
+  in.keys.n = n;
+  in.leaf = leaf_size;
+  in.bucket_size = bucket_size;
   Handle* h = nullptr;
-  if ((rc = build_structure(in, leaf_size, bucket_size, s, &h))) return rc;
+  if ((rc = build_sets(&in, 1, BuildOptions{}, s, &h))) return rc;
   *out = reinterpret_cast<recsplit_t*>(h);
+  return RECSPLIT_OK;
+}
+
+int recsplit_build_batch(const recsplit_keyset_t* sets, uint32_t count, void* stream, recsplit_t** outs) {
+  if (count && (!sets || !outs)) return fail(RECSPLIT_E_INVALID, "sets or outs is NULL");
+  std::vector<SetInput> in(count);
+  std::vector<uint32_t> leaves;
+  for (uint32_t i = 0; i < count; i++) {
+    outs[i] = nullptr;
+    const recsplit_keyset_t& k = sets[i];
+    recsplit_t* dummy = nullptr;
+    int rc = check_build_args(k.n, k.leaf_size, k.bucket_size, &dummy);
+    if (rc) return rc;
+    if (k.n) {
+      const bool u64 = k.keys != nullptr;
+      if (u64 ? !on_device(k.keys) : (!k.bytes || !k.offsets || !on_device(k.bytes) || !on_device(k.offsets)))
+        return fail(RECSPLIT_E_INVALID, "batched builds need the keys of every set in device memory");
+    }
+    in[i].keys.u64 = k.keys;
+    in[i].keys.bytes = k.keys ? nullptr : k.bytes;
+    in[i].keys.offsets = k.keys ? nullptr : k.offsets;
+    in[i].keys.n = k.n;
+    in[i].leaf = k.leaf_size;
+    in[i].bucket_size = k.bucket_size;
+  }
+  std::vector<Handle*> hs(count, nullptr);
+  BuildOptions opt;
+  opt.use_graph = true;
+  int rc = build_sets(in.data(), count, opt, static_cast<cudaStream_t>(stream), hs.data());
+  if (rc) return rc;
+  for (uint32_t i = 0; i < count; i++) outs[i] = reinterpret_cast<recsplit_t*>(hs[i]);
+  return RECSPLIT_OK;
+}
+
+int recsplit_lookup_batch(const recsplit_t* const* hs, uint32_t count, const uint32_t* ids, const uint64_t* keys,
+                          uint64_t q, uint64_t* out, void* stream) {
+  if (!q) return RECSPLIT_OK;
+  if (!hs || !ids || !keys || !out || !count) return fail(RECSPLIT_E_INVALID, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<View> views(count);
+  for (uint32_t i = 0; i < count; i++) {
+    if (!hs[i]) return fail(RECSPLIT_E_INVALID, "structure is NULL");
+    views[i] = make_view(*as_handle(hs[i]));
+  }
+  const bool dev = on_device(keys);
+  if (on_device(ids) != dev || on_device(out) != dev)
+    return fail(RECSPLIT_E_INVALID, "ids, keys and out must all be host or all device memory");
+  Staged v, k, d, o;
+  int rc;
+  if ((rc = v.from(views.data(), count * sizeof(View), false, s))) return rc;
+  if (!dev) {
+    if ((rc = k.from(keys, q * sizeof(uint64_t), false, s)) || (rc = d.from(ids, q * sizeof(uint32_t), false, s)))
+      return rc;
+    o.s = s;
+    if ((rc = pool_alloc(&o.dev, q * sizeof(uint64_t), s))) return rc;
+    o.owned = true;
+  } else {
+    k.dev = const_cast<uint64_t*>(keys);
+    d.dev = const_cast<uint32_t*>(ids);
+    o.dev = out;
+  }
+  if ((rc = lookup_many(static_cast<const View*>(v.dev), static_cast<const uint32_t*>(d.dev),
+                        static_cast<const uint64_t*>(k.dev), q, static_cast<uint64_t*>(o.dev), s)))
+    return rc;
+  if (!dev) RS_CUDA(cudaMemcpyAsync(out, o.dev, q * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  RS_CUDA(cudaStreamSynchronize(s));  // the staged views are released after the lookups
   return RECSPLIT_OK;
 }
 
@@ -274,20 +345,20 @@ int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t**
   h->layout = L;
   cudaGetDevice(&h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMalloc(&h->d_blob, len) != cudaSuccess ||
-      cudaMalloc(&h->d_table, T.device_words.size() * sizeof(uint64_t)) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(h->d_blob);
+  h->blob_mem = std::make_shared<DeviceMem>();
+  h->table_mem = std::make_shared<DeviceMem>();
+  if ((rc = pool_alloc(&h->blob_mem->p, len, s)) ||
+      (rc = pool_alloc(&h->table_mem->p, T.device_words.size() * sizeof(uint64_t), s))) {
     delete h;
-    return fail(RECSPLIT_E_NOMEM, "device allocation failed");
+    return rc;
   }
+  h->d_blob = static_cast<uint64_t*>(h->blob_mem->p);
+  h->d_table = static_cast<uint64_t*>(h->table_mem->p);
   if (cudaMemcpyAsync(h->d_blob, buf, len, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(h->d_table, T.device_words.data(), T.device_words.size() * sizeof(uint64_t),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     rc = cuda_fail(cudaGetLastError(), "deserialize");
-    cudaFree(h->d_blob);
-    cudaFree(h->d_table);
     delete h;
     return rc;
   }
@@ -315,10 +386,7 @@ int recsplit_stats(const recsplit_t* hp, recsplit_stats_t* st) {
 
 void recsplit_free(recsplit_t* hp) {
   if (!hp) return;
-  Handle* h = as_handle(hp);
-  cudaFree(h->d_blob);
-  cudaFree(h->d_table);
-  delete h;
+  delete as_handle(hp);  // device memory goes with the last structure that shares it
 }
 
 const char* recsplit_strerror(int code) {

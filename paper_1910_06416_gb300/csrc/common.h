@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -71,11 +72,19 @@ struct Tables {
 int build_tables(uint32_t leaf, uint64_t mmax, Tables* out, std::string* err);
 
 // ---------------------------------------------------------------- handle
+// Device memory released when the last structure that uses it is freed
+// (the structures of one batched build share one arena).
+struct DeviceMem {
+  void* p = nullptr;
+  ~DeviceMem();
+};
+
 struct Handle {
   uint64_t header[kHeaderWords];
   Layout layout;
+  std::shared_ptr<DeviceMem> blob_mem, table_mem;
   uint64_t* d_blob = nullptr;   // serialized structure, device resident
-  uint64_t* d_table = nullptr;  // device_words of the tables
+  uint64_t* d_table = nullptr;  // device tables (kTableWords per node size)
   uint64_t ncodes = 0;
   int device = 0;
 };
@@ -135,37 +144,55 @@ struct KeyInput {
   uint64_t n = 0;
 };
 
-int build_structure(const KeyInput& in, uint32_t leaf, uint32_t bucket_size, cudaStream_t s, Handle** out);
-int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s);
+// One key set of a (batched) build: keys in device memory and parameters.
+struct SetInput {
+  KeyInput keys;
+  uint32_t leaf = 0;
+  uint32_t bucket_size = 0;
+};
 
-// Search launchers (search.cu).
+struct BuildOptions {
+  bool use_graph = false;  // capture the search and length phases in a CUDA graph
+};
+
+// Builds one structure per set in one pass over all sets (out[i] for set i).
+// KeyInput pointers must be device memory.
+int build_sets(const SetInput* sets, uint32_t count, const BuildOptions& opt, cudaStream_t s, Handle** out);
+int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s);
+int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
+                cudaStream_t s);
+
+// Search launchers (search.cu).  A node's `depth` word holds its depth in
+// bits 0..7 and the parameter class (leaf size index) of its set in bits 8..15.
 struct Node {
   uint32_t start;  // first key (index into the key array of its depth parity)
   uint32_t m;      // keys
   uint32_t slot;   // code slot of this node (preorder within its bucket)
-  uint32_t depth;  // depth in the tree, root = 0
+  uint32_t depth;  // depth | class << 8
 };
+constexpr uint32_t kDepthMask = 0xFF;
+constexpr int kMaxClasses = 25;
 
 struct SearchArgs {
-  uint64_t* keys[2];         // key arrays (x ^ x >> 30) by depth parity
-  uint64_t* seeds;           // one per code slot
-  uint32_t* sizes;           // node size per code slot
-  const uint64_t* table;     // device tables
-  Node* split_in;            // split nodes of this level
+  uint64_t* keys[2];                      // key arrays (x ^ x >> 30) by depth parity
+  uint64_t* seeds;                        // one per code slot
+  uint32_t* sizes;                        // node size per code slot
+  const uint64_t* table[kMaxClasses];     // device tables per class
+  uint32_t leaf_of[kMaxClasses];          // leaf size per class
+  Node* split_in;                         // split nodes of this level
   uint32_t* split_in_count;
-  Node* split_out;           // split nodes of the next level
+  Node* split_out;                        // split nodes of the next level
   uint32_t* split_out_count;
-  Node* leaves_full;         // leaves of exactly `leaf` keys
-  uint32_t* leaves_full_count;
-  Node* leaves_part;         // leaves of 2 .. leaf-1 keys
-  uint32_t* leaves_part_count;
-  uint32_t* work_counter;    // dynamic scheduling counter (zeroed per launch)
-  int* error;                // first error code
-  uint32_t leaf;
-  uint64_t lower, upper;     // strategy units
+  Node* full_q[kMaxClasses];              // leaves of exactly the class's leaf size
+  uint32_t* full_n;                       // per class
+  Node* part_q[kMaxClasses];              // leaves of 2 .. leaf-1 keys
+  uint32_t* part_n;                       // per class
+  uint32_t* work_counter;                 // dynamic scheduling counter (zeroed per launch)
+  int* error;                             // first error code
+  uint32_t cls;                           // class of a leaf launch
 };
 
-int launch_split_level(const SearchArgs& a, uint64_t max_m, uint64_t max_nodes, int sm_count, cudaStream_t s);
-int launch_leaves(const SearchArgs& a, uint64_t max_nodes, int sm_count, cudaStream_t s);
+int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s);
+int launch_leaves(const SearchArgs& a, uint32_t leaf, int sm_count, cudaStream_t s);
 
 }  // namespace rs

@@ -77,7 +77,31 @@ __global__ void k_lookup_bytes(View v, const uint8_t* __restrict__ bytes, const 
   }
 }
 
+__global__ void k_lookup_many(const View* __restrict__ views, const uint32_t* __restrict__ ids,
+                              const uint64_t* __restrict__ keys, uint64_t q, uint64_t* __restrict__ out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t hi, lo;
+    signature_u64(__ldg(keys + i), hi, lo);
+    out[i] = lookup_one(views[__ldg(ids + i)], hi, lo);
+  }
+}
+
 }  // namespace
+
+int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
+                cudaStream_t s) {
+  if (q == 0) return RECSPLIT_OK;
+  int dev = 0, sms = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int block = 256;
+  const uint64_t want = (q + block - 1) / block;
+  const unsigned grid = static_cast<unsigned>(want < uint64_t(sms) * 64 ? want : uint64_t(sms) * 64);
+  k_lookup_many<<<grid, block, 0, s>>>(d_views, d_ids, d_keys, q, d_out);
+  count_launch();
+  RS_CUDA(cudaGetLastError());
+  return RECSPLIT_OK;
+}
 
 View make_view(const Handle& h) {
   View v;

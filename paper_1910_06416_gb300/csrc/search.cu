@@ -158,13 +158,14 @@ __device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, 
 
 // Emits the children of a split node with at least two keys into the queues
 // of full leaves, partial leaves or next-level splits (one warp).
-__device__ void emit_children(const SearchArgs& a, const Node& nd, uint32_t unit, uint32_t fanout,
-                              uint32_t lane) {
+__device__ void emit_children(const SearchArgs& a, const Node& nd, const uint64_t* table, uint32_t leaf,
+                              uint32_t unit, uint32_t fanout, uint32_t lane) {
   const uint32_t t = lane;
   const uint32_t k = t + 1 < fanout ? unit : nd.m - unit * (fanout - 1);
   const bool valid = t < fanout && k >= 2;
-  const uint32_t cls = k == a.leaf ? 0 : (k < a.leaf ? 1 : 2);
-  const uint32_t unit_codes = static_cast<uint32_t>(a.table[kTableWords * unit] >> 32);
+  const uint32_t kind = k == leaf ? 0 : (k < leaf ? 1 : 2);
+  const uint32_t c_of_node = nd.depth >> 8;
+  const uint32_t unit_codes = static_cast<uint32_t>(table[kTableWords * unit] >> 32);
   Node child;
   child.start = nd.start + t * unit;
   child.m = k;
@@ -172,12 +173,12 @@ __device__ void emit_children(const SearchArgs& a, const Node& nd, uint32_t unit
   child.depth = nd.depth + 1;
 #pragma unroll
   for (uint32_t c = 0; c < 3; c++) {
-    const bool mine = valid && cls == c;
+    const bool mine = valid && kind == c;
     const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, mine);
     if (!ballot) continue;
     const uint32_t leader = __ffs(ballot) - 1;
-    Node* q = c == 0 ? a.leaves_full : (c == 1 ? a.leaves_part : a.split_out);
-    uint32_t* cnt = c == 0 ? a.leaves_full_count : (c == 1 ? a.leaves_part_count : a.split_out_count);
+    Node* q = c == 0 ? a.full_q[c_of_node] : (c == 1 ? a.part_q[c_of_node] : a.split_out);
+    uint32_t* cnt = c == 0 ? a.full_n + c_of_node : (c == 1 ? a.part_n + c_of_node : a.split_out_count);
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(cnt, __popc(ballot));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
@@ -203,7 +204,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     const uint32_t idx = task[gid];
     if (idx >= total) break;
     const Node nd = a.split_in[idx];
-    const uint64_t w1 = a.table[kTableWords * nd.m + 1];
+    const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
+    const uint64_t* table = a.table[cls];
+    const uint64_t w1 = table[kTableWords * nd.m + 1];
     SplitParams sp;
     sp.m = nd.m;
     sp.unit = static_cast<uint32_t>(w1);
@@ -216,11 +219,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
     // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
     const int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
-    const uint64_t stall = stall_threshold(a.table, nd.m);
-    const uint64_t limit = trial_limit(a.table, nd.m);
+    const uint64_t stall = stall_threshold(table, nd.m);
+    const uint64_t limit = trial_limit(table, nd.m);
 
-    const uint64_t* src = a.keys[nd.depth & 1] + nd.start;
-    uint64_t* dst = a.keys[(nd.depth + 1) & 1] + nd.start;
+    const uint64_t* src = a.keys[depth & 1] + nd.start;
+    uint64_t* dst = a.keys[(depth + 1) & 1] + nd.start;
     const bool in_smem = nd.m <= cap;
     if (in_smem)
       for (uint32_t j = tig; j < nd.m; j += gthreads) mine[j] = src[j];
@@ -229,9 +232,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     group_sync(gid, gwarps);
 
     if (in_smem)
-      split_search(mine, sp, mode, nd.depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+      split_search(mine, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
     else
-      split_search(src, sp, mode, nd.depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+      split_search(src, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
     group_sync(gid, gwarps);
 
     const uint64_t seed = best[gid];
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
         a.sizes[nd.slot] = nd.m;
       }
       // partition the keys into the children's ranges of the other array
-      const uint64_t kp = family_key(seed, nd.depth);
+      const uint64_t kp = family_key(seed, depth);
       const uint64_t* from = in_smem ? mine : src;
       for (uint32_t j = tig; j < nd.m; j += gthreads) {
         const uint64_t x = from[j];
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
         else
           set_error(a.error, RECSPLIT_E_INVALID);  // unreachable for a correct split
       }
-      if (wig == 0) emit_children(a, nd, sp.unit, sp.fanout, lane);
+      if (wig == 0) emit_children(a, nd, table, a.leaf_of[cls], sp.unit, sp.fanout, lane);
     }
     group_sync(gid, gwarps);
   }
@@ -292,8 +295,9 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t gid = warp / gwarps, wig = warp % gwarps;
   const bool leader = wig == 0 && lane == 0;
-  const Node* queue = FULL ? a.leaves_full : a.leaves_part;
-  const uint32_t total = FULL ? *a.leaves_full_count : *a.leaves_part_count;
+  const Node* queue = FULL ? a.full_q[a.cls] : a.part_q[a.cls];
+  const uint32_t total = FULL ? a.full_n[a.cls] : a.part_n[a.cls];
+  const uint64_t* table = a.table[a.cls];
 
   for (;;) {
     if (leader) task[gid] = *reinterpret_cast<volatile int*>(a.error) ? total : atomicAdd(a.work_counter, chunk);
@@ -304,7 +308,8 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
     for (uint32_t idx = first; idx < last; idx++) {
       const Node nd = queue[idx];
       const uint32_t m = FULL ? LMAX : nd.m;
-      const uint64_t* src = a.keys[nd.depth & 1] + nd.start;
+      const uint32_t depth = nd.depth & kDepthMask;
+      const uint64_t* src = a.keys[depth & 1] + nd.start;
       uint64_t x[LMAX];
       uint32_t keep[LMAX];
 #pragma unroll
@@ -314,8 +319,8 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
       }
       if (leader) best[gid] = ~0ull;
       group_sync(gid, gwarps);
-      const uint64_t stall = stall_threshold(a.table, m);
-      const uint64_t limit = trial_limit(a.table, m);
+      const uint64_t stall = stall_threshold(table, m);
+      const uint64_t limit = trial_limit(table, m);
       bool checked = false;
       for (uint64_t base = uint64_t(wig) * 32;; base += uint64_t(gwarps) * 32) {
         if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(&best[gid]))) break;
@@ -341,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
             break;
           }
         }
-        const uint64_t kp = family_key(base + lane, nd.depth);
+        const uint64_t kp = family_key(base + lane, depth);
         const bool ok = FULL ? leaf_trial_full<LMAX>(x, kp) : leaf_trial_part<LMAX>(x, keep, m, kp);
         const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
         if (hits) {
@@ -396,13 +401,12 @@ constexpr FullLauncher kFull[25] = {
 
 }  // namespace
 
-int launch_split_level(const SearchArgs& a, uint64_t max_m, uint64_t max_nodes, int sm_count, cudaStream_t s) {
-  (void)max_nodes;
+int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s) {
   // heavier nodes get more warps: fewer nodes per level and longer searches
   uint32_t gwarps = 1;
   if (max_m >= 256)
     gwarps = 8;
-  else if (max_m >= 64 && a.leaf >= 12)
+  else if (max_m >= 64 && max_leaf >= 12)
     gwarps = 2;
   const uint32_t groups = kWarps / gwarps;
   const size_t budget = 96 * 1024;
@@ -420,15 +424,15 @@ int launch_split_level(const SearchArgs& a, uint64_t max_m, uint64_t max_nodes, 
   return RECSPLIT_OK;
 }
 
-int launch_leaves(const SearchArgs& a, uint64_t max_nodes, int sm_count, cudaStream_t s) {
-  (void)max_nodes;
-  if (a.leaf < 2) return RECSPLIT_OK;
-  const uint32_t gwarps = a.leaf >= 12 ? 4 : 1;
-  const uint32_t chunk = a.leaf >= 12 ? 1 : 4;
-  int rc = kFull[a.leaf](a, gwarps, chunk, sm_count, s);
+int launch_leaves(const SearchArgs& a, uint32_t leaf, int sm_count, cudaStream_t s) {
+  if (leaf < 2) return RECSPLIT_OK;
+  const uint32_t gwarps = leaf >= 12 ? 4 : 1;
+  const uint32_t chunk = leaf >= 12 ? 1 : 4;
+  int rc = kFull[leaf](a, gwarps, chunk, sm_count, s);
   if (rc) return rc;
-  if (a.leaf <= 8) return launch_leaf_kernel<8, false>(a, gwarps, chunk, sm_count, s);
-  if (a.leaf <= 16) return launch_leaf_kernel<16, false>(a, gwarps, chunk, sm_count, s);
+  if (leaf == 2) return RECSPLIT_OK;  // no leaves between 2 and leaf - 1
+  if (leaf <= 8) return launch_leaf_kernel<8, false>(a, gwarps, chunk, sm_count, s);
+  if (leaf <= 16) return launch_leaf_kernel<16, false>(a, gwarps, chunk, sm_count, s);
   return launch_leaf_kernel<24, false>(a, gwarps, chunk, sm_count, s);
 }
 

@@ -168,3 +168,37 @@ def device_byte_queries(keys: ByteKeys, idx: np.ndarray, device="cuda"):
         mask = col[None, :] < qlen[c0:c1, None]
         out[int(offsets[c0].item()):int(offsets[c1].item())] = rows[mask]
     return out, offsets
+
+
+def device_splitmix64(seed: int, count: int, start: int = 0, device="cuda"):
+    """splitmix64(seed) outputs start .. start+count-1 computed on `device`
+    (int64 tensor holding the same bits as splitmix64()).  torch has no
+    unsigned 64-bit arithmetic, so logical right shifts are masked."""
+    import torch
+
+    def u2s(x):
+        return x - (1 << 64) if x >= 1 << 63 else x
+
+    k = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    z = k * u2s(int(WEYL)) + u2s(seed & 0xFFFFFFFFFFFFFFFF)
+
+    def shr(x, s):
+        return (x >> s) & ((1 << (64 - s)) - 1)
+
+    z = z ^ shr(z, 30)
+    z = z * u2s(0xBF58476D1CE4E5B9)
+    z = z ^ shr(z, 27)
+    z = z * u2s(0x94D049BB133111EB)
+    return z ^ shr(z, 31)
+
+
+def batch_sets(count: int, lo: int, hi: int, seed: int, leaves=(5, 8, 12), buckets=(5, 100, 2000)):
+    """The key-set plan of a batch: per set its size (log-uniform in
+    [lo, hi)), its (leaf, bucket) pair (uniform over the product of `leaves`
+    and `buckets`), and the seed of its keys.  Set i's 64-bit keys are
+    u64_keys(size_i, seed_i)."""
+    sizes = log_uniform_sizes(count, lo, hi, seed)
+    pick = _mulhi_small(splitmix64(seed ^ 0x243F6A8885A308D3, count), len(leaves) * len(buckets)).astype(np.int64)
+    combos = [(l, b) for l in leaves for b in buckets]
+    seeds = splitmix64(seed ^ 0x13198A2E03707344, count)
+    return [(int(sizes[i]), combos[int(pick[i])][0], combos[int(pick[i])][1], int(seeds[i])) for i in range(count)]

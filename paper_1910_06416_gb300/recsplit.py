@@ -41,6 +41,11 @@ class Profile(C.Structure):
                 ("launches", C.c_uint32), ("split_levels", C.c_uint32)]
 
 
+class KeySet(C.Structure):
+    _fields_ = [("keys", C.c_void_p), ("bytes", C.c_void_p), ("offsets", C.c_void_p), ("n", C.c_uint64),
+                ("leaf_size", C.c_uint32), ("bucket_size", C.c_uint32)]
+
+
 class RecSplitError(RuntimeError):
     def __init__(self, code: int, where: str):
         lib = _lib
@@ -78,12 +83,15 @@ def lib():
             L.recsplit_set_profiling.argtypes = [i]
             L.recsplit_last_profile.argtypes = [C.POINTER(Profile)]
             L.recsplit_lookup_u64_static.argtypes = [p, p, u64, p, p]
+            L.recsplit_build_batch.argtypes = [p, u32, p, p]
+            L.recsplit_lookup_batch.argtypes = [p, u32, p, p, u64, p, p]
             L.recsplit_launch_count.argtypes = []
             L.recsplit_launch_count.restype = u64
             for name in ("recsplit_build_u64", "recsplit_build", "recsplit_build_bytes", "recsplit_lookup_u64",
                          "recsplit_lookup", "recsplit_lookup_bytes", "recsplit_serialize", "recsplit_deserialize",
                          "recsplit_stats", "recsplit_golomb_rice_params", "recsplit_set_profiling",
-                         "recsplit_last_profile", "recsplit_lookup_u64_static"):
+                         "recsplit_last_profile", "recsplit_lookup_u64_static", "recsplit_build_batch",
+                         "recsplit_lookup_batch"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -151,6 +159,31 @@ def recsplit_build_bytes(data, offsets, leaf_size: int, bucket_size: int, stream
 def recsplit_lookup_u64(h: int, keys, out, stream=None) -> None:
     _check(lib().recsplit_lookup_u64(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
            "recsplit_lookup_u64")
+
+
+def recsplit_build_batch(sets, stream=None) -> list[int]:
+    """Build one structure per set in one pass.  `sets`: sequence of
+    (keys, leaf_size, bucket_size) for 64-bit keys or
+    (bytes, offsets, leaf_size, bucket_size) for byte strings (device arrays)."""
+    arr = (KeySet * max(1, len(sets)))()
+    for i, st in enumerate(sets):
+        if len(st) == 3:
+            keys, leaf, b = st
+            arr[i] = KeySet(_ptr(keys), None, None, _count(keys), leaf, b)
+        else:
+            data, offs, leaf, b = st
+            arr[i] = KeySet(None, _ptr(data), _ptr(offs), _count(offs) - 1, leaf, b)
+    outs = (C.c_void_p * max(1, len(sets)))()
+    _check(lib().recsplit_build_batch(C.cast(arr, C.c_void_p), len(sets), _stream(stream), C.cast(outs, C.c_void_p)),
+           "recsplit_build_batch")
+    return [outs[i] for i in range(len(sets))]
+
+
+def recsplit_lookup_batch(handles, ids, keys, out, stream=None) -> None:
+    """out[i] = lookup of keys[i] in handles[ids[i]]."""
+    hs = (C.c_void_p * max(1, len(handles)))(*handles)
+    _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _ptr(ids), _ptr(keys), _count(keys),
+                                       _ptr(out), _stream(stream)), "recsplit_lookup_batch")
 
 
 STATIC_LOOKUP_MAX = 1 << 20
