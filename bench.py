@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--leaf", type=int, default=8)
     ap.add_argument("--bucket", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -119,11 +121,11 @@ class ClockSampler:
         return out
 
 
-def traffic_from_profiles(kernel_tag):
+def traffic_from_profiles(kernel_tag, source="search.cu"):
     """DRAM bytes per launch recorded by an ncu capture summary, if the kernel
     source has not changed since (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_1910_06416_gb300", "csrc", "search.cu")
+    src = os.path.join(ROOT, "paper_1910_06416_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -153,6 +155,70 @@ def cpu_baseline(a, keys_np):
     return {"value": ns / dt, "unit": "keys/s", "cores": threads, "kind": "oracle",
             "sample": f"oracle build of the first {ns} keys of the workload (same l, b; {threads} threads), "
                       f"{dt:.1f} s"}
+
+
+def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5):
+    """Continuous-batching server under Poisson arrivals (mean `rate`/s):
+    half builds of log-uniform 10^4..10^7 byte-string keys (slices of the
+    key pool), half lookups of log-uniform 10^3..10^6 member queries against
+    a resident structure.  Latency is submission to completion."""
+    rng = np.random.default_rng(seed)
+    srv = rs.recsplit_server_create(hbm_budget_bytes=64 << 30)
+    npool = keys.n
+    times, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            break
+        times.append(t)
+    is_build = rng.random(len(times)) < 0.5
+    bsize = np.minimum(np.floor(10 ** rng.uniform(4, 7, len(times))).astype(np.int64), npool)
+    qsize = np.floor(10 ** rng.uniform(3, 6, len(times))).astype(np.int64)
+    pick = rng.random(len(times))
+    resident = []  # (structure id, first key, keys)
+    info, outs, done = {}, {}, []
+
+    def drain(wait_ms=0):
+        for c in rs.recsplit_server_poll(srv, 1024, wait_ms):
+            done.append(c)
+            kind, start, n = info[c["request_id"]]
+            if kind == 0 and c["status"] == 0:
+                resident.append((c["structure_id"], start, n))
+            outs.pop(c["request_id"], None)
+
+    t0 = time.perf_counter()
+    for i, te in enumerate(times):
+        drain()
+        delay = t0 + te - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        if not is_build[i] and resident:
+            sid, start, n = resident[int(pick[i] * len(resident))]
+            q = int(min(qsize[i], n))
+            a0 = start + int(rng.integers(0, n - q + 1))
+            out = np.empty(q, dtype=np.uint64)
+            rid = rs.recsplit_server_submit_lookup_bytes(srv, sid, keys.data, keys.offsets[a0:a0 + q + 1], out)
+            info[rid] = (1, a0, q)
+            outs[rid] = out
+        else:
+            n = int(bsize[i])
+            start = int(rng.integers(0, npool - n + 1))
+            rid = rs.recsplit_server_submit_build_bytes(srv, keys.data, keys.offsets[start:start + n + 1], leaf, bucket)
+            info[rid] = (0, start, n)
+    while len(done) < len(info):
+        drain(50)
+    wall = time.perf_counter() - t0
+    rs.recsplit_server_destroy(srv)
+    res = {"seconds": wall, "rate_hz": rate, "requests": len(done)}
+    for kind, name in ((0, "build"), (1, "lookup")):
+        lat = np.array([c["latency_ms"] for c in done if c["kind"] == kind and c["status"] == 0])
+        items = sum(c["items"] for c in done if c["kind"] == kind and c["status"] == 0)
+        res[name] = {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                     "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                     "items_per_s": items / wall,
+                     "mean_batch": float(np.mean([c["batch_size"] for c in done if c["kind"] == kind] or [0]))}
+    res["failed"] = sum(1 for c in done if c["status"] != 0)
+    return res
 
 
 def run_reference(a):
@@ -263,29 +329,41 @@ def run_ours(a):
     value = world * a.n * a.steps / (sb / 1000.0)
     lookup_qps = world * a.queries * a.steps / (sl / 1000.0)
 
-    # roofline of the dominant kernel (integer issue bound; no tensor cores)
+    # rooflines: searches are integer-issue bound (no tensor cores, no floating
+    # point); the lookup reads query strings from HBM and writes indices
     leaf_ms = sum(p["ms_leaf"] for p in profs) / len(profs)
     split_ms = sum(p["ms_split"] for p in profs) / len(profs)
-    leaf_ops = profs[-1]["leaf_evals"] * OPS_PER_LEAF_EVAL
-    split_ops = profs[-1]["split_evals"] * OPS_PER_SPLIT_EVAL
+    look_ms = sl / a.steps
     peak_ops = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
-    if leaf_ms >= split_ms:
-        kernel, achieved = "leaf_search", leaf_ops / (leaf_ms / 1000.0)
-    else:
-        kernel, achieved = "split_search", split_ops / (split_ms / 1000.0)
-    tag = f"{kernel}_strings_n{a.n}_l{a.leaf}_b{a.bucket}"
-    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic_from_profiles(tag),
-                "peak_source": "152 SMs x 128 lanes/clk x 2070 MHz (issue-limited 32-bit integer instructions)",
-                "ops_per_eval": OPS_PER_LEAF_EVAL if kernel == "leaf_search" else OPS_PER_SPLIT_EVAL}
-    lookup_bytes = int(qdata.numel()) + 8 * (a.queries + 1) + 8 * a.queries
-    look_gbs = lookup_bytes / (sl / a.steps / 1000.0) / 1e9
+    peak_src = "152 SMs x 128 lanes/clk x 2070 MHz (issue-limited 32-bit integer instructions; derived)"
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    tag = f"strings_n{a.n}_l{a.leaf}_b{a.bucket}"
+    lookup_bytes = int(qdata.numel()) + 8 * (a.queries + 1) + 8 * a.queries
+    rooflines = {
+        "leaf_search": {"bound": "alu", "ms": leaf_ms,
+                        "achieved": profs[-1]["leaf_evals"] * OPS_PER_LEAF_EVAL / (leaf_ms / 1e3) / 1e12,
+                        "peak": peak_ops / 1e12, "unit": "Tops/s", "ops_per_eval": OPS_PER_LEAF_EVAL,
+                        "peak_source": peak_src, "traffic": traffic_from_profiles(f"leaf_search_{tag}")},
+        "split_search": {"bound": "alu", "ms": split_ms,
+                         "achieved": profs[-1]["split_evals"] * OPS_PER_SPLIT_EVAL / (split_ms / 1e3) / 1e12,
+                         "peak": peak_ops / 1e12, "unit": "Tops/s", "ops_per_eval": OPS_PER_SPLIT_EVAL,
+                         "peak_source": peak_src, "traffic": traffic_from_profiles(f"split_search_{tag}")},
+        "lookup": {"bound": "hbm", "ms": look_ms, "achieved": lookup_bytes / (look_ms / 1e3) / 1e9, "peak": hbm_peak,
+                   "unit": "GB/s", "bytes_per_query": lookup_bytes / a.queries,
+                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                   "traffic": traffic_from_profiles(f"lookup_{tag}", "lookup.cu")},
+    }
+    for r in rooflines.values():
+        r["frac"] = r["achieved"] / r["peak"]
+        if r["traffic"] is not None:
+            r["traffic"] = r["traffic"] * (a.queries / 1_000_000 if r is rooflines["lookup"] else 1.0)
+    kernel = max(rooflines, key=lambda k: rooflines[k]["ms"])
+    roofline = dict(rooflines[kernel], kernel=kernel)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -311,16 +389,16 @@ def run_ours(a):
                 "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": dict(workload_config(a), parallelism=f"replicas{world}"),
-                "lookup": {"value": lookup_qps, "unit": "queries/s",
-                           "hbm": {"achieved": look_gbs, "peak": hbm_peak, "unit": "GB/s",
-                                   "frac": look_gbs / hbm_peak, "bytes_per_query": lookup_bytes / a.queries}},
+                "lookup": {"value": lookup_qps, "unit": "queries/s"},
                 "build_ms": statistics.median(build_ms), "lookup_ms": statistics.median(look_ms),
                 "phases_ms": {k: statistics.median(p[k] for p in profs)
                               for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")},
                 "work": {k: profs[-1][k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes",
                                                    "leaf_trials", "leaf_evals")},
-                "bits_per_key": stats["bits_per_key"], "roofline": roofline, "e2e": e2e,
+                "bits_per_key": stats["bits_per_key"], "roofline": roofline, "rooflines": rooflines, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks}
+        if a.serve_seconds > 0:
+            line["serve"] = serve_run(rs, keys, a.serve_seconds, a.serve_rate, a.leaf, a.bucket)
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a, keys)
         print(json.dumps(line), flush=True)

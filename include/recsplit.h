@@ -171,6 +171,70 @@ int recsplit_last_profile(recsplit_profile_t* out);
 /* Kernels launched by the library on the calling host thread so far. */
 uint64_t recsplit_launch_count(void);
 
+/* ---------------------------------------------------------------------
+ * Serving engine: a request loop that builds and queries structures as
+ * requests arrive, keeping the structures resident in device memory.  Builds
+ * waiting while others run are admitted in arrival order as the memory budget
+ * allows and built together in one multi-set build; lookups waiting are served
+ * together in one batched launch on a stream of their own, overlapping the
+ * builds.  Every result equals that of the same request served alone.
+ * Buffers passed to submit calls are host memory (the engine copies inputs
+ * to the device when it starts the request) and must stay valid (inputs
+ * unchanged, outputs untouched) until the request completes.
+ * The paper has no serving layer; this is the interface of the library.
+ * --------------------------------------------------------------------- */
+typedef struct recsplit_server recsplit_server_t;
+
+typedef struct recsplit_server_config {
+  uint64_t hbm_budget_bytes;  /* device bytes for resident structures + builds in flight (0: 64 GiB) */
+  uint32_t max_build_batch;   /* builds per device round (0: 64)                               */
+  uint64_t max_lookup_batch;  /* queries per lookup launch (0: 2^26)                            */
+} recsplit_server_config_t;
+
+typedef struct recsplit_completion {
+  uint64_t request_id;
+  uint64_t structure_id; /* builds: the id lookups use (= request_id) on success */
+  uint64_t items;        /* keys built or queries answered                    */
+  int32_t kind;          /* 0 build, 1 lookup                                 */
+  int32_t status;        /* RECSPLIT_OK or an error code                      */
+  double queue_ms;       /* submission to the start of its device round       */
+  double latency_ms;     /* submission to completion (host clock)             */
+  uint32_t batch_size;   /* requests served in the same device round          */
+} recsplit_completion_t;
+
+typedef struct recsplit_server_stats {
+  uint64_t resident_structures;
+  uint64_t resident_bytes;
+  uint64_t in_flight_bytes;
+  uint64_t queued_builds;
+  uint64_t queued_lookups;
+  uint64_t keys_built;
+  uint64_t queries_answered;
+} recsplit_server_stats_t;
+
+/* Starts a server on the current device (cfg may be NULL for defaults). */
+int recsplit_server_create(const recsplit_server_config_t* cfg, recsplit_server_t** out);
+/* Stops the workers after the queued requests and frees everything. */
+void recsplit_server_destroy(recsplit_server_t* srv);
+/* Queues a build (leaf_size, bucket_size as for recsplit_build_u64). */
+int recsplit_server_submit_build_u64(recsplit_server_t* srv, const uint64_t* keys, uint64_t n, uint32_t leaf_size,
+                                     uint32_t bucket_size, uint64_t* request_id);
+int recsplit_server_submit_build_bytes(recsplit_server_t* srv, const uint8_t* bytes, const uint64_t* offsets,
+                                       uint64_t n, uint32_t leaf_size, uint32_t bucket_size, uint64_t* request_id);
+/* Queues q lookups against a resident structure; results go to out. */
+int recsplit_server_submit_lookup_u64(recsplit_server_t* srv, uint64_t structure_id, const uint64_t* keys, uint64_t q,
+                                      uint64_t* out, uint64_t* request_id);
+int recsplit_server_submit_lookup_bytes(recsplit_server_t* srv, uint64_t structure_id, const uint8_t* bytes,
+                                        const uint64_t* offsets, uint64_t q, uint64_t* out, uint64_t* request_id);
+/* Takes up to cap completions (waiting up to wait_ms for the first). */
+int recsplit_server_poll(recsplit_server_t* srv, recsplit_completion_t* out, uint32_t cap, uint32_t* count,
+                         int wait_ms);
+/* Borrows a resident structure (valid until released; do not free it). */
+int recsplit_server_structure(recsplit_server_t* srv, uint64_t structure_id, const recsplit_t** out);
+/* Drops a resident structure, returning its memory to the budget. */
+int recsplit_server_release(recsplit_server_t* srv, uint64_t structure_id);
+int recsplit_server_stats(recsplit_server_t* srv, recsplit_server_stats_t* st);
+
 /* Largest number of keys one recsplit_lookup_u64_static call accepts. */
 #define RECSPLIT_STATIC_LOOKUP_MAX (1u << 20)
 

@@ -161,6 +161,8 @@ int build_sets(const SetInput* sets, uint32_t count, const BuildOptions& opt, cu
 int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s);
 int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
                 cudaStream_t s);
+int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t* d_bytes, const uint64_t* d_offsets,
+                      uint64_t q, uint64_t* d_out, cudaStream_t s);
 
 // Search launchers (search.cu).  A node's `depth` word holds its depth in
 // bits 0..7 and the parameter class (leaf size index) of its set in bits 8..15.

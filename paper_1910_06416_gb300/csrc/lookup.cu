@@ -86,7 +86,33 @@ __global__ void k_lookup_many(const View* __restrict__ views, const uint32_t* __
   }
 }
 
+__global__ void k_lookup_many_bytes(const View* __restrict__ views, const uint32_t* __restrict__ ids,
+                                    const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ offsets,
+                                    uint64_t q, uint64_t* __restrict__ out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
+    uint64_t hi, lo;
+    signature_bytes(bytes + o0, o1 - o0, hi, lo);
+    out[i] = lookup_one(views[__ldg(ids + i)], hi, lo);
+  }
+}
+
 }  // namespace
+
+int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t* d_bytes, const uint64_t* d_offsets,
+                      uint64_t q, uint64_t* d_out, cudaStream_t s) {
+  if (q == 0) return RECSPLIT_OK;
+  int dev = 0, sms = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int block = 256;
+  const uint64_t want = (q + block - 1) / block;
+  const unsigned grid = static_cast<unsigned>(want < uint64_t(sms) * 64 ? want : uint64_t(sms) * 64);
+  k_lookup_many_bytes<<<grid, block, 0, s>>>(d_views, d_ids, d_bytes, d_offsets, q, d_out);
+  count_launch();
+  RS_CUDA(cudaGetLastError());
+  return RECSPLIT_OK;
+}
 
 int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
                 cudaStream_t s) {

@@ -46,6 +46,22 @@ class KeySet(C.Structure):
                 ("leaf_size", C.c_uint32), ("bucket_size", C.c_uint32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_build_batch", C.c_uint32), ("max_lookup_batch", C.c_uint64)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("structure_id", C.c_uint64), ("items", C.c_uint64),
+                ("kind", C.c_int32), ("status", C.c_int32), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
+                ("batch_size", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("resident_structures", C.c_uint64), ("resident_bytes", C.c_uint64), ("in_flight_bytes", C.c_uint64),
+                ("queued_builds", C.c_uint64), ("queued_lookups", C.c_uint64), ("keys_built", C.c_uint64),
+                ("queries_answered", C.c_uint64)]
+
+
 class RecSplitError(RuntimeError):
     def __init__(self, code: int, where: str):
         lib = _lib
@@ -84,6 +100,17 @@ def lib():
             L.recsplit_last_profile.argtypes = [C.POINTER(Profile)]
             L.recsplit_lookup_u64_static.argtypes = [p, p, u64, p, p]
             L.recsplit_build_batch.argtypes = [p, u32, p, p]
+            L.recsplit_server_create.argtypes = [p, p]
+            L.recsplit_server_destroy.argtypes = [p]
+            L.recsplit_server_destroy.restype = None
+            L.recsplit_server_submit_build_u64.argtypes = [p, p, u64, u32, u32, p]
+            L.recsplit_server_submit_build_bytes.argtypes = [p, p, p, u64, u32, u32, p]
+            L.recsplit_server_submit_lookup_u64.argtypes = [p, u64, p, u64, p, p]
+            L.recsplit_server_submit_lookup_bytes.argtypes = [p, u64, p, p, u64, p, p]
+            L.recsplit_server_poll.argtypes = [p, p, u32, p, i]
+            L.recsplit_server_structure.argtypes = [p, u64, p]
+            L.recsplit_server_release.argtypes = [p, u64]
+            L.recsplit_server_stats.argtypes = [p, p]
             L.recsplit_lookup_batch.argtypes = [p, u32, p, p, u64, p, p]
             L.recsplit_launch_count.argtypes = []
             L.recsplit_launch_count.restype = u64
@@ -91,7 +118,10 @@ def lib():
                          "recsplit_lookup", "recsplit_lookup_bytes", "recsplit_serialize", "recsplit_deserialize",
                          "recsplit_stats", "recsplit_golomb_rice_params", "recsplit_set_profiling",
                          "recsplit_last_profile", "recsplit_lookup_u64_static", "recsplit_build_batch",
-                         "recsplit_lookup_batch"):
+                         "recsplit_lookup_batch", "recsplit_server_create", "recsplit_server_submit_build_u64",
+                         "recsplit_server_submit_build_bytes", "recsplit_server_submit_lookup_u64",
+                         "recsplit_server_submit_lookup_bytes", "recsplit_server_poll", "recsplit_server_structure",
+                         "recsplit_server_release", "recsplit_server_stats"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -184,6 +214,72 @@ def recsplit_lookup_batch(handles, ids, keys, out, stream=None) -> None:
     hs = (C.c_void_p * max(1, len(handles)))(*handles)
     _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _ptr(ids), _ptr(keys), _count(keys),
                                        _ptr(out), _stream(stream)), "recsplit_lookup_batch")
+
+
+# ---------------------------------------------------------------- serving
+def recsplit_server_create(hbm_budget_bytes=0, max_build_batch=0, max_lookup_batch=0) -> int:
+    cfg = ServerConfig(hbm_budget_bytes, max_build_batch, max_lookup_batch)
+    h = C.c_void_p()
+    _check(lib().recsplit_server_create(C.byref(cfg), C.byref(h)), "recsplit_server_create")
+    return h.value
+
+
+def recsplit_server_destroy(srv: int) -> None:
+    lib().recsplit_server_destroy(C.c_void_p(srv))
+
+
+def recsplit_server_submit_build_u64(srv: int, keys, leaf_size: int, bucket_size: int) -> int:
+    rid = C.c_uint64()
+    _check(lib().recsplit_server_submit_build_u64(C.c_void_p(srv), _ptr(keys), _count(keys), leaf_size, bucket_size,
+                                                  C.byref(rid)), "recsplit_server_submit_build_u64")
+    return rid.value
+
+
+def recsplit_server_submit_build_bytes(srv: int, data, offsets, leaf_size: int, bucket_size: int) -> int:
+    rid = C.c_uint64()
+    _check(lib().recsplit_server_submit_build_bytes(C.c_void_p(srv), _ptr(data), _ptr(offsets), _count(offsets) - 1,
+                                                    leaf_size, bucket_size, C.byref(rid)),
+           "recsplit_server_submit_build_bytes")
+    return rid.value
+
+
+def recsplit_server_submit_lookup_u64(srv: int, structure_id: int, keys, out) -> int:
+    rid = C.c_uint64()
+    _check(lib().recsplit_server_submit_lookup_u64(C.c_void_p(srv), structure_id, _ptr(keys), _count(keys), _ptr(out),
+                                                   C.byref(rid)), "recsplit_server_submit_lookup_u64")
+    return rid.value
+
+
+def recsplit_server_submit_lookup_bytes(srv: int, structure_id: int, data, offsets, out) -> int:
+    rid = C.c_uint64()
+    _check(lib().recsplit_server_submit_lookup_bytes(C.c_void_p(srv), structure_id, _ptr(data), _ptr(offsets),
+                                                     _count(offsets) - 1, _ptr(out), C.byref(rid)),
+           "recsplit_server_submit_lookup_bytes")
+    return rid.value
+
+
+def recsplit_server_poll(srv: int, cap: int = 1024, wait_ms: int = 0) -> list[dict]:
+    arr = (Completion * cap)()
+    cnt = C.c_uint32()
+    _check(lib().recsplit_server_poll(C.c_void_p(srv), C.cast(arr, C.c_void_p), cap, C.byref(cnt), wait_ms),
+           "recsplit_server_poll")
+    return [{name: getattr(arr[i], name) for name, _ in Completion._fields_} for i in range(cnt.value)]
+
+
+def recsplit_server_structure(srv: int, structure_id: int) -> int:
+    h = C.c_void_p()
+    _check(lib().recsplit_server_structure(C.c_void_p(srv), structure_id, C.byref(h)), "recsplit_server_structure")
+    return h.value
+
+
+def recsplit_server_release(srv: int, structure_id: int) -> None:
+    _check(lib().recsplit_server_release(C.c_void_p(srv), structure_id), "recsplit_server_release")
+
+
+def recsplit_server_stats(srv: int) -> dict:
+    st = ServerStats()
+    _check(lib().recsplit_server_stats(C.c_void_p(srv), C.byref(st)), "recsplit_server_stats")
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
 
 
 STATIC_LOOKUP_MAX = 1 << 20
