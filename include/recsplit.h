@@ -254,6 +254,31 @@ int recsplit_server_stats(recsplit_server_t* srv, recsplit_server_stats_t* st);
  * after the results are in out. */
 int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
 
+/* Launch shapes of the seed searches for one leaf size.  They change only
+ * speed: every search returns the first successful index whatever the shape.
+ *  leaf_warps:   warps that search one leaf together (1, 2, 4 or 8 of a CTA)
+ *  leaf_chunk:   leaves a group takes from the work queue at a time (1..64)
+ *  leaf_seeds_per_lane: indices each lane tests per round (1, 2 or 4)
+ *  split_warps[k]: warps per split node for levels whose largest node has
+ *                <64 (k=0), <256 (k=1) or more (k=2) keys (1, 2, 4 or 8) */
+typedef struct recsplit_tuning {
+  uint32_t leaf_warps;
+  uint32_t leaf_chunk;
+  uint32_t leaf_seeds_per_lane;
+  uint32_t split_warps[3];
+} recsplit_tuning_t;
+
+/* Current launch shapes for leaf size l (process-wide). */
+int recsplit_get_tuning(uint32_t leaf_size, recsplit_tuning_t* out);
+/* Installs launch shapes for leaf size l (process-wide; validated). */
+int recsplit_set_tuning(uint32_t leaf_size, const recsplit_tuning_t* t);
+/* Autotuner: builds a seeded synthetic sample of about sample_keys 64-bit keys
+ * with leaf size l and bucket size b under candidate launch shapes, times the
+ * leaf and split searches with CUDA events, installs the fastest shapes for l
+ * and returns them in *out (may be NULL).  Uses the current device. */
+int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_keys, void* stream,
+                      recsplit_tuning_t* out);
+
 /* Golomb-Rice parameters of nodes of 0 .. m_hi keys for leaf size l
  * (Sec. 5.4 Eq. gr with the probabilities of Sec. 5.1 / 5.2, and the integer
  * rule of Sec. 7.2 from 2^16 keys on): out[m] for m in [0, m_hi], host

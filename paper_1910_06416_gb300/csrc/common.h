@@ -197,4 +197,9 @@ struct SearchArgs {
 int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s);
 int launch_leaves(const SearchArgs& a, uint32_t leaf, int sm_count, cudaStream_t s);
 
+// Launch shapes of the searches for one leaf size (see recsplit_tuning_t).
+recsplit_tuning_t tuning_for(uint32_t leaf);
+void set_tuning_for(uint32_t leaf, const recsplit_tuning_t& t);
+recsplit_tuning_t default_tuning(uint32_t leaf);
+
 }  // namespace rs

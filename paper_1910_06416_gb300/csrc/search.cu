@@ -12,6 +12,7 @@
 // result is deterministic and independent of G).  Nodes are handed out by an
 // atomic counter (persistent CTAs), the heaviest levels with larger groups.
 #include <algorithm>
+#include <mutex>
 
 #include "device.cuh"
 
@@ -289,7 +290,7 @@ constexpr int leaf_min_blocks(int l) { return l <= 5 ? 6 : (l <= 8 ? 5 : (l <= 1
 
 template <int LMAX, bool FULL>
 __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(SearchArgs a, uint32_t gwarps,
-                                                                            uint32_t chunk) {
+                                                                            uint32_t chunk, uint32_t spl) {
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -322,7 +323,10 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
       const uint64_t stall = stall_threshold(table, m);
       const uint64_t limit = trial_limit(table, m);
       bool checked = false;
-      for (uint64_t base = uint64_t(wig) * 32;; base += uint64_t(gwarps) * 32) {
+      // a round of a warp covers the spl * 32 indices from base; lane L tests
+      // base + j * 32 + L for j < spl
+      const uint64_t span = uint64_t(spl) * 32;
+      for (uint64_t base = uint64_t(wig) * span;; base += uint64_t(gwarps) * span) {
         if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(&best[gid]))) break;
         if (base >= limit) {
           if (lane == 0) {
@@ -346,11 +350,15 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
             break;
           }
         }
-        const uint64_t kp = family_key(base + lane, depth);
-        const bool ok = FULL ? leaf_trial_full<LMAX>(x, kp) : leaf_trial_part<LMAX>(x, keep, m, kp);
-        const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
-        if (hits) {
-          if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), base + __ffs(hits) - 1);
+        uint64_t found = ~0ull;
+        for (uint32_t j = 0; j < spl; j++) {
+          const uint64_t kp = family_key(base + j * 32 + lane, depth);
+          const bool ok = FULL ? leaf_trial_full<LMAX>(x, kp) : leaf_trial_part<LMAX>(x, keep, m, kp);
+          const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+          if (hits && found == ~0ull) found = base + j * 32 + __ffs(hits) - 1;
+        }
+        if (found != ~0ull) {
+          if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), found);
           break;
         }
       }
@@ -374,24 +382,24 @@ int persistent_grid(K kernel, size_t smem, int sm_count, int* blocks) {
 }
 
 template <int LMAX, bool FULL>
-int launch_leaf_kernel(const SearchArgs& a, uint32_t gwarps, uint32_t chunk, int sm_count, cudaStream_t s) {
+int launch_leaf_kernel(const SearchArgs& a, const recsplit_tuning_t& t, int sm_count, cudaStream_t s) {
   auto kern = k_leaves<LMAX, FULL>;
   int blocks = 0;
   int rc = persistent_grid(kern, 0, sm_count, &blocks);
   if (rc) return rc;
   RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
-  kern<<<blocks, kThreads, 0, s>>>(a, gwarps, chunk);
+  kern<<<blocks, kThreads, 0, s>>>(a, t.leaf_warps, t.leaf_chunk, t.leaf_seeds_per_lane);
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;
 }
 
 template <int L>
-int launch_full(const SearchArgs& a, uint32_t gw, uint32_t chunk, int sm, cudaStream_t s) {
-  return launch_leaf_kernel<L, true>(a, gw, chunk, sm, s);
+int launch_full(const SearchArgs& a, const recsplit_tuning_t& t, int sm, cudaStream_t s) {
+  return launch_leaf_kernel<L, true>(a, t, sm, s);
 }
 
-typedef int (*FullLauncher)(const SearchArgs&, uint32_t, uint32_t, int, cudaStream_t);
+typedef int (*FullLauncher)(const SearchArgs&, const recsplit_tuning_t&, int, cudaStream_t);
 constexpr FullLauncher kFull[25] = {
     nullptr,         nullptr,         launch_full<2>,  launch_full<3>,  launch_full<4>,
     launch_full<5>,  launch_full<6>,  launch_full<7>,  launch_full<8>,  launch_full<9>,
@@ -401,13 +409,40 @@ constexpr FullLauncher kFull[25] = {
 
 }  // namespace
 
+// ---------------------------------------------------------------- tuning
+namespace {
+std::mutex g_tune_mu;
+recsplit_tuning_t g_tune[kMaxLeaf + 1];
+bool g_tuned[kMaxLeaf + 1] = {};
+}  // namespace
+
+recsplit_tuning_t default_tuning(uint32_t leaf) {
+  recsplit_tuning_t t;
+  t.leaf_warps = leaf >= 12 ? 4 : 1;
+  t.leaf_chunk = leaf >= 12 ? 1 : 4;
+  t.leaf_seeds_per_lane = 1;
+  t.split_warps[0] = 1;
+  t.split_warps[1] = leaf >= 12 ? 2 : 1;
+  t.split_warps[2] = 8;
+  return t;
+}
+
+recsplit_tuning_t tuning_for(uint32_t leaf) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (leaf > kMaxLeaf || !g_tuned[leaf]) return default_tuning(leaf);
+  return g_tune[leaf];
+}
+
+void set_tuning_for(uint32_t leaf, const recsplit_tuning_t& t) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[leaf] = t;
+  g_tuned[leaf] = true;
+}
+
 int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s) {
   // heavier nodes get more warps: fewer nodes per level and longer searches
-  uint32_t gwarps = 1;
-  if (max_m >= 256)
-    gwarps = 8;
-  else if (max_m >= 64 && max_leaf >= 12)
-    gwarps = 2;
+  const recsplit_tuning_t t = tuning_for(max_leaf);
+  const uint32_t gwarps = t.split_warps[max_m >= 256 ? 2 : (max_m >= 64 ? 1 : 0)];
   const uint32_t groups = kWarps / gwarps;
   const size_t budget = 96 * 1024;
   uint64_t cap = std::min<uint64_t>(max_m, budget / (groups * sizeof(uint64_t)));
@@ -426,14 +461,13 @@ int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, i
 
 int launch_leaves(const SearchArgs& a, uint32_t leaf, int sm_count, cudaStream_t s) {
   if (leaf < 2) return RECSPLIT_OK;
-  const uint32_t gwarps = leaf >= 12 ? 4 : 1;
-  const uint32_t chunk = leaf >= 12 ? 1 : 4;
-  int rc = kFull[leaf](a, gwarps, chunk, sm_count, s);
+  const recsplit_tuning_t t = tuning_for(leaf);
+  int rc = kFull[leaf](a, t, sm_count, s);
   if (rc) return rc;
   if (leaf == 2) return RECSPLIT_OK;  // no leaves between 2 and leaf - 1
-  if (leaf <= 8) return launch_leaf_kernel<8, false>(a, gwarps, chunk, sm_count, s);
-  if (leaf <= 16) return launch_leaf_kernel<16, false>(a, gwarps, chunk, sm_count, s);
-  return launch_leaf_kernel<24, false>(a, gwarps, chunk, sm_count, s);
+  if (leaf <= 8) return launch_leaf_kernel<8, false>(a, t, sm_count, s);
+  if (leaf <= 16) return launch_leaf_kernel<16, false>(a, t, sm_count, s);
+  return launch_leaf_kernel<24, false>(a, t, sm_count, s);
 }
 
 }  // namespace rs

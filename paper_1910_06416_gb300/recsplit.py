@@ -62,6 +62,16 @@ class ServerStats(C.Structure):
                 ("queries_answered", C.c_uint64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("leaf_warps", C.c_uint32), ("leaf_chunk", C.c_uint32), ("leaf_seeds_per_lane", C.c_uint32),
+                ("split_warps", C.c_uint32 * 3)]
+
+
+def _tuning_dict(t: Tuning) -> dict:
+    return {"leaf_warps": t.leaf_warps, "leaf_chunk": t.leaf_chunk, "leaf_seeds_per_lane": t.leaf_seeds_per_lane,
+            "split_warps": list(t.split_warps)}
+
+
 class RecSplitError(RuntimeError):
     def __init__(self, code: int, where: str):
         lib = _lib
@@ -100,6 +110,9 @@ def lib():
             L.recsplit_last_profile.argtypes = [C.POINTER(Profile)]
             L.recsplit_lookup_u64_static.argtypes = [p, p, u64, p, p]
             L.recsplit_build_batch.argtypes = [p, u32, p, p]
+            L.recsplit_get_tuning.argtypes = [u32, p]
+            L.recsplit_set_tuning.argtypes = [u32, p]
+            L.recsplit_autotune.argtypes = [u32, u32, u64, p, p]
             L.recsplit_server_create.argtypes = [p, p]
             L.recsplit_server_destroy.argtypes = [p]
             L.recsplit_server_destroy.restype = None
@@ -121,7 +134,8 @@ def lib():
                          "recsplit_lookup_batch", "recsplit_server_create", "recsplit_server_submit_build_u64",
                          "recsplit_server_submit_build_bytes", "recsplit_server_submit_lookup_u64",
                          "recsplit_server_submit_lookup_bytes", "recsplit_server_poll", "recsplit_server_structure",
-                         "recsplit_server_release", "recsplit_server_stats"):
+                         "recsplit_server_release", "recsplit_server_stats",
+                         "recsplit_get_tuning", "recsplit_set_tuning", "recsplit_autotune"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -214,6 +228,26 @@ def recsplit_lookup_batch(handles, ids, keys, out, stream=None) -> None:
     hs = (C.c_void_p * max(1, len(handles)))(*handles)
     _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _ptr(ids), _ptr(keys), _count(keys),
                                        _ptr(out), _stream(stream)), "recsplit_lookup_batch")
+
+
+# ---------------------------------------------------------------- tuning
+def recsplit_get_tuning(leaf_size: int) -> dict:
+    t = Tuning()
+    _check(lib().recsplit_get_tuning(leaf_size, C.byref(t)), "recsplit_get_tuning")
+    return _tuning_dict(t)
+
+
+def recsplit_set_tuning(leaf_size: int, tuning: dict) -> None:
+    t = Tuning(tuning["leaf_warps"], tuning["leaf_chunk"], tuning["leaf_seeds_per_lane"],
+               (C.c_uint32 * 3)(*tuning["split_warps"]))
+    _check(lib().recsplit_set_tuning(leaf_size, C.byref(t)), "recsplit_set_tuning")
+
+
+def recsplit_autotune(leaf_size: int, bucket_size: int, sample_keys: int = 1 << 20, stream=None) -> dict:
+    t = Tuning()
+    _check(lib().recsplit_autotune(leaf_size, bucket_size, sample_keys, _stream(stream), C.byref(t)),
+           "recsplit_autotune")
+    return _tuning_dict(t)
 
 
 # ---------------------------------------------------------------- serving

@@ -59,3 +59,16 @@ def test_golomb_rice_table_equals_oracle(rs, orc):
         ms = [65536, 70000, 100000, 250001]
         got = rs.recsplit_golomb_rice_params(leaf, max(ms))
         assert [int(got[m]) for m in ms] == [orc.golomb_rice(leaf, m) for m in ms]
+
+
+def test_tuning_shapes_are_validated(rs):
+    t = rs.recsplit_get_tuning(8)
+    assert t["leaf_warps"] in (1, 2, 4, 8)
+    for bad in ({"leaf_warps": 3}, {"leaf_chunk": 0}, {"leaf_chunk": 65}, {"leaf_seeds_per_lane": 8},
+                {"split_warps": [1, 16, 8]}):
+        tt = dict(t, **bad)
+        with pytest.raises(rs.RecSplitError) as e:
+            rs.recsplit_set_tuning(8, tt)
+        assert e.value.code == rs.E_INVALID
+    with pytest.raises(rs.RecSplitError):
+        rs.recsplit_get_tuning(25)
