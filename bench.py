@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--leaf", type=int, default=8)
     ap.add_argument("--bucket", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="strings", choices=["strings", "u64", "batch"],
+                    help="strings: byte-string keys (default workload); u64: 64-bit keys (seed 0 for leaf 5, "
+                         "seed 2 otherwise); batch: 4096 sets of log-uniform sizes with mixed leaf/bucket sizes")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
@@ -277,7 +280,7 @@ def run_ours(a):
 
     # launch shapes of the searches for this leaf size, picked by the autotuner
     # on a seeded synthetic sample (untimed; results do not depend on them)
-    tuning = rs.recsplit_autotune(a.leaf, a.bucket, 1 << 20, stream.cuda_stream)
+    tuning = rs.recsplit_autotune(a.leaf, a.bucket, a.n, stream.cuda_stream)
     rs.recsplit_set_profiling(True)
 
     def step():
@@ -411,10 +414,153 @@ def run_ours(a):
     return 0
 
 
+def run_u64(a):
+    """64-bit keys (n, leaf, bucket from the flags): build keys/s and member
+    lookups/s, with the same rooflines as the default workload."""
+    import torch
+
+    from paper_1910_06416_gb300 import build as lib_build, inputs
+    import paper_1910_06416_gb300.recsplit as rs
+
+    lib_build.build()
+    rs.lib()
+    dev = torch.device("cuda", 0)
+    seed = 0 if a.leaf == 5 else 2
+    keys_np = inputs.u64_keys(a.n, seed)
+    keys = torch.from_numpy(keys_np.view(np.int64)).to(dev)
+    qidx = torch.from_numpy(inputs.query_indices(a.n, a.queries, seed)).to(dev)
+    queries = keys[qidx]
+    del qidx
+    out = torch.empty(a.queries, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    tuning = rs.recsplit_autotune(a.leaf, a.bucket, a.n, stream.cuda_stream)
+    rs.recsplit_set_profiling(True)
+    bt, lt, profs = [], [], []
+    for step in range(a.warmup + a.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        h = rs.recsplit_build_u64(keys, a.leaf, a.bucket, stream.cuda_stream)
+        e1.record(stream)
+        rs.recsplit_lookup_u64(h, queries, out, stream.cuda_stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if step >= a.warmup:
+            bt.append(e0.elapsed_time(e1))
+            lt.append(e1.elapsed_time(e2))
+            profs.append(rs.recsplit_last_profile())
+        stats = rs.recsplit_stats(h)
+        rs.recsplit_free(h)
+    line = {"metric": "build keys/s (64-bit keys)", "value": a.n / (statistics.median(bt) / 1e3), "unit": "keys/s",
+            "workload": "u64", "n": a.n, "leaf_size": a.leaf, "bucket_size": a.bucket, "seed": seed,
+            "build_ms": statistics.median(bt), "lookup": {"value": a.queries / (statistics.median(lt) / 1e3),
+                                                          "unit": "queries/s", "queries": a.queries},
+            "phases_ms": {k: statistics.median(p[k] for p in profs)
+                          for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")},
+            "work": {k: profs[-1][k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes",
+                                               "leaf_trials", "leaf_evals")},
+            "bits_per_key": stats["bits_per_key"], "tuning": tuning}
+    peak_ops = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    for kind, ops in (("leaf", OPS_PER_LEAF_EVAL), ("split", OPS_PER_SPLIT_EVAL)):
+        ms = line["phases_ms"][f"ms_{kind}"]
+        if ms > 0:
+            line[f"{kind}_search_frac_of_issue_peak"] = line["work"][f"{kind}_evals"] * ops / (ms / 1e3) / peak_ops
+    if not a.no_cpu_baseline:
+        from oracle import oracle
+        threads = os.cpu_count() or 1
+        ns = min(a.n, 200_000 if a.leaf <= 8 else (20_000 if a.leaf <= 12 else 2_000))
+        t0 = time.perf_counter()
+        oracle.build_u64(keys_np[:ns], a.leaf, a.bucket, threads=threads)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ns / dt, "unit": "keys/s", "cores": threads, "kind": "oracle",
+                                "sample": f"oracle build of the first {ns} keys ({threads} threads), {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(a):
+    """4096 independent structures (sizes log-uniform in [10^3, 10^6), seed 3,
+    leaf sizes {5, 8, 12} x bucket sizes {5, 100, 2000}) built in one batched
+    pass, against one build per launch; then 10^9 batched lookups."""
+    import torch
+
+    from paper_1910_06416_gb300 import build as lib_build, inputs
+    import paper_1910_06416_gb300.recsplit as rs
+
+    lib_build.build()
+    rs.lib()
+    dev = torch.device("cuda", 0)
+    plan = inputs.batch_sets(4096, 1000, 1000000, 3)
+    keys = [inputs.device_splitmix64(sd, n, device=dev) for n, _, _, sd in plan]
+    total = sum(p[0] for p in plan)
+    stream = torch.cuda.current_stream(dev)
+    for leaf in sorted({p[1] for p in plan}):
+        b = max((p for p in plan if p[1] == leaf), key=lambda p: p[0])[2]
+        rs.recsplit_autotune(leaf, b, 1 << 20, stream.cuda_stream)
+    sets = [(k, l, b) for k, (n, l, b, _) in zip(keys, plan)]
+    batch_t, bits = [], 0
+    for step in range(a.warmup + a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = rs.recsplit_build_batch(sets, stream.cuda_stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if step >= a.warmup:
+            batch_t.append(dt)
+        if step == a.warmup + a.steps - 1:
+            bits = sum(rs.recsplit_stats(h)["total_bits"] for h in hs)
+            handles = hs
+        else:
+            for h in hs:
+                rs.recsplit_free(h)
+    # one build per launch, same sets
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    singles_bits = 0
+    for k, l, b in sets:
+        h = rs.recsplit_build_u64(k, l, b, stream.cuda_stream)
+        singles_bits += rs.recsplit_stats(h)["total_bits"]
+        rs.recsplit_free(h)
+    torch.cuda.synchronize()
+    single_t = time.perf_counter() - t0
+    # 10^9 batched lookups (set uniform, then a key uniform in the set)
+    q, chunk = 1_000_000_000, 100_000_000
+    sizes = torch.tensor([p[0] for p in plan], device=dev, dtype=torch.int64)
+    flat = torch.cat(keys)
+    offs = torch.zeros(len(plan) + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(sizes, 0, out=offs[1:])
+    out = torch.empty(chunk, dtype=torch.int64, device=dev)
+    look_ms = 0.0
+    for c0 in range(0, q, chunk):
+        r = inputs.device_splitmix64(0xC4C4, 2 * chunk, start=2 * c0, device=dev)
+        ids = ((r[0::2] >> 1) % len(plan)).to(torch.int32)
+        qk = flat[offs[ids.long()] + (r[1::2] >> 1) % sizes[ids.long()]]
+        del r
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs.recsplit_lookup_batch(handles, ids, qk, out, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        look_ms += e0.elapsed_time(e1)
+    for h in handles:
+        rs.recsplit_free(h)
+    line = {"metric": "batched build keys/s vs one build per launch (4096 structures)", "workload": "batch",
+            "value": total / statistics.median(batch_t), "unit": "keys/s", "keys": total, "sets": len(plan),
+            "batch_s": statistics.median(batch_t), "one_per_launch": {"value": total / single_t, "unit": "keys/s",
+                                                                     "seconds": single_t},
+            "bits_per_key": bits / total, "bits_per_key_one_per_launch": singles_bits / total,
+            "lookup": {"value": q / (look_ms / 1e3), "unit": "queries/s", "queries": q}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "u64":
+        return run_u64(a)
+    if a.workload == "batch":
+        return run_batch(a)
     return run_ours(a)
 
 

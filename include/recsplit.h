@@ -258,7 +258,7 @@ int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64
  * speed: every search returns the first successful index whatever the shape.
  *  leaf_warps:   warps that search one leaf together (1, 2, 4 or 8 of a CTA)
  *  leaf_chunk:   leaves a group takes from the work queue at a time (1..64)
- *  leaf_seeds_per_lane: indices each lane tests per round (1, 2 or 4)
+ *  leaf_seeds_per_lane: indices each lane tests per round (1, 2, 4 or 8)
  *  split_warps[k]: warps per split node for levels whose largest node has
  *                <64 (k=0), <256 (k=1) or more (k=2) keys (1, 2, 4 or 8) */
 typedef struct recsplit_tuning {

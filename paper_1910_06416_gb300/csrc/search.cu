@@ -275,6 +275,56 @@ __device__ __forceinline__ bool leaf_trial_full(const uint64_t (&x)[L], uint64_t
   return seen == (L == 32 ? ~0u : ((1u << L) - 1));
 }
 
+// Two-phase round of a warp over the indices base + j * 32 + lane, j < spl,
+// for a leaf of exactly L keys.  Phase 1 maps the first H keys: an index whose
+// first H values are not distinct cannot be a bijection.  The survivors are
+// compacted, in index order, into the warp's shared buffer with their
+// partial one-hot masks; phase 2 finishes them on the last L - H keys, 32 at
+// a time.  The first survivor that completes 2^L - 1 is the smallest
+// bijective index of the round.  Returns it, or ~0 if the round has none.
+__host__ __device__ constexpr int leaf_first_half(int l) { return (l + 1) / 2; }
+constexpr uint32_t kMaxSpl = 8;
+
+template <int L>
+__device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L], uint64_t base, uint32_t depth,
+                                                         uint32_t spl, uint32_t lane, uint2* surv) {
+  constexpr int H = leaf_first_half(L);
+  constexpr uint32_t full = L == 32 ? ~0u : ((1u << L) - 1);
+  uint32_t nsurv = 0;
+  for (uint32_t j = 0; j < spl; j++) {
+    const uint32_t off = j * 32 + lane;
+    const uint64_t kp = family_key(base + off, depth);
+    uint32_t seen = 0;
+#pragma unroll
+    for (int i = 0; i < H; i++) seen |= 1u << phi_pre(x[i], kp, L);
+    const bool ok = __popc(seen) == H;
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok) surv[nsurv + __popc(b & ((1u << lane) - 1))] = make_uint2(off, seen);
+    nsurv += __popc(b);
+  }
+  __syncwarp();
+  for (uint32_t t0 = 0; t0 < nsurv; t0 += 32) {
+    const uint32_t t = t0 + lane;
+    bool ok = false;
+    if (t < nsurv) {
+      const uint2 e = surv[t];
+      const uint64_t kp = family_key(base + e.x, depth);
+      uint32_t seen = e.y;
+#pragma unroll
+      for (int i = H; i < L; i++) seen |= 1u << phi_pre(x[i], kp, L);
+      ok = seen == full;
+    }
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+    if (b) {
+      const uint64_t win = base + surv[t0 + __ffs(b) - 1].x;
+      __syncwarp();
+      return win;
+    }
+  }
+  __syncwarp();
+  return ~0ull;
+}
+
 // Leaf of m < LMAX keys: slots j >= m contribute nothing.
 template <int LMAX>
 __device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const uint32_t (&keep)[LMAX], uint32_t m,
@@ -286,13 +336,15 @@ __device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const
 }
 
 // Blocks per SM the register budget must allow (keys live in registers).
-constexpr int leaf_min_blocks(int l) { return l <= 5 ? 6 : (l <= 8 ? 5 : (l <= 16 ? 4 : 3)); }
+__host__ __device__ constexpr int leaf_min_blocks(int l) { return l <= 5 ? 6 : (l <= 8 ? 5 : (l <= 16 ? 4 : 3)); }
 
 template <int LMAX, bool FULL>
 __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(SearchArgs a, uint32_t gwarps,
                                                                             uint32_t chunk, uint32_t spl) {
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
+  constexpr bool kTwoPhase = FULL && LMAX >= 4;
+  __shared__ uint2 surv[kTwoPhase ? kWarps : 1][kTwoPhase ? 32 * kMaxSpl : 1];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t gid = warp / gwarps, wig = warp % gwarps;
   const bool leader = wig == 0 && lane == 0;
@@ -351,11 +403,15 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
           }
         }
         uint64_t found = ~0ull;
-        for (uint32_t j = 0; j < spl; j++) {
-          const uint64_t kp = family_key(base + j * 32 + lane, depth);
-          const bool ok = FULL ? leaf_trial_full<LMAX>(x, kp) : leaf_trial_part<LMAX>(x, keep, m, kp);
-          const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
-          if (hits && found == ~0ull) found = base + j * 32 + __ffs(hits) - 1;
+        if (kTwoPhase) {
+          found = leaf_round_two_phase<LMAX>(x, base, depth, spl, lane, surv[warp]);
+        } else {
+          for (uint32_t j = 0; j < spl; j++) {
+            const uint64_t kp = family_key(base + j * 32 + lane, depth);
+            const bool ok = FULL ? leaf_trial_full<LMAX>(x, kp) : leaf_trial_part<LMAX>(x, keep, m, kp);
+            const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+            if (hits && found == ~0ull) found = base + j * 32 + __ffs(hits) - 1;
+          }
         }
         if (found != ~0ull) {
           if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), found);
@@ -420,7 +476,7 @@ recsplit_tuning_t default_tuning(uint32_t leaf) {
   recsplit_tuning_t t;
   t.leaf_warps = leaf >= 12 ? 4 : 1;
   t.leaf_chunk = leaf >= 12 ? 1 : 4;
-  t.leaf_seeds_per_lane = 1;
+  t.leaf_seeds_per_lane = leaf >= 4 ? 4 : 1;
   t.split_warps[0] = 1;
   t.split_warps[1] = leaf >= 12 ? 2 : 1;
   t.split_warps[2] = 8;

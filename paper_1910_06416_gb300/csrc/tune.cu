@@ -21,7 +21,7 @@ __global__ void k_sample_keys(uint64_t* keys, uint64_t n, uint64_t seed) {
 
 bool valid_tuning(const recsplit_tuning_t& t) {
   auto pow2_upto = [](uint32_t v, uint32_t hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
-  if (!pow2_upto(t.leaf_warps, 8) || t.leaf_chunk < 1 || t.leaf_chunk > 64 || !pow2_upto(t.leaf_seeds_per_lane, 4))
+  if (!pow2_upto(t.leaf_warps, 8) || t.leaf_chunk < 1 || t.leaf_chunk > 64 || !pow2_upto(t.leaf_seeds_per_lane, 8))
     return false;
   for (uint32_t w : t.split_warps)
     if (!pow2_upto(w, 8)) return false;
@@ -119,7 +119,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
       if (ms < leaf_ms) leaf_ms = ms, best = t;
     }
     if (rc) break;
-    for (uint32_t k : {1u, 2u, 4u}) {
+    for (uint32_t k : {1u, 2u, 4u, 8u}) {
       recsplit_tuning_t t = best;
       t.leaf_seeds_per_lane = k;
       double ms;

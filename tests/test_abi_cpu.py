@@ -64,7 +64,7 @@ def test_golomb_rice_table_equals_oracle(rs, orc):
 def test_tuning_shapes_are_validated(rs):
     t = rs.recsplit_get_tuning(8)
     assert t["leaf_warps"] in (1, 2, 4, 8)
-    for bad in ({"leaf_warps": 3}, {"leaf_chunk": 0}, {"leaf_chunk": 65}, {"leaf_seeds_per_lane": 8},
+    for bad in ({"leaf_warps": 3}, {"leaf_chunk": 0}, {"leaf_chunk": 65}, {"leaf_seeds_per_lane": 16},
                 {"split_warps": [1, 16, 8]}):
         tt = dict(t, **bad)
         with pytest.raises(rs.RecSplitError) as e:

@@ -22,7 +22,7 @@ def rs():
 
 SHAPES = [
     {"leaf_warps": 1, "leaf_chunk": 1, "leaf_seeds_per_lane": 1, "split_warps": [1, 1, 1]},
-    {"leaf_warps": 8, "leaf_chunk": 64, "leaf_seeds_per_lane": 4, "split_warps": [8, 8, 8]},
+    {"leaf_warps": 8, "leaf_chunk": 64, "leaf_seeds_per_lane": 8, "split_warps": [8, 8, 8]},
     {"leaf_warps": 2, "leaf_chunk": 16, "leaf_seeds_per_lane": 2, "split_warps": [2, 4, 2]},
 ]
 
@@ -44,7 +44,7 @@ def test_structures_identical_under_every_shape(rs, orc, leaf, b, n):
 def test_autotuner_installs_valid_shapes(rs, orc):
     t = rs.recsplit_autotune(8, 100, 1 << 18)
     assert rs.recsplit_get_tuning(8) == t
-    assert t["leaf_warps"] in (1, 2, 4, 8) and t["leaf_seeds_per_lane"] in (1, 2, 4)
+    assert t["leaf_warps"] in (1, 2, 4, 8) and t["leaf_seeds_per_lane"] in (1, 2, 4, 8)
     keys = inputs.u64_keys(30000, 7)
     got = rs.Structure.build_u64(keys, 8, 100).serialize()
     assert np.array_equal(got, orc.build_u64(keys, 8, 100))
