@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--leaf", type=int, default=8)
     ap.add_argument("--bucket", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="strings", choices=["strings", "u64", "batch"],
+    ap.add_argument("--workload", default="strings", choices=["strings", "u64", "batch", "sweep"],
                     help="strings: byte-string keys (default workload); u64: 64-bit keys (seed 0 for leaf 5, "
                          "seed 2 otherwise); batch: 4096 sets of log-uniform sizes with mixed leaf/bucket sizes")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -553,6 +553,39 @@ def run_batch(a):
     return 0
 
 
+def run_sweep(a):
+    """Space and construction time over leaf sizes 2..18 and bucket sizes
+    {5, 100, 2000} (64-bit keys, seed 4): the data of the paper's space
+    figure and its construction-time trend (about e per unit of leaf size)."""
+    import torch
+
+    from paper_1910_06416_gb300 import build as lib_build, inputs
+    import paper_1910_06416_gb300.recsplit as rs
+
+    lib_build.build()
+    rs.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    rs.recsplit_set_profiling(True)
+    rows = []
+    for leaf in range(2, 19):
+        n = 1_000_000 if leaf <= 14 else (200_000 if leaf <= 16 else 20_000)
+        keys = torch.from_numpy(inputs.u64_keys(n, 4).view(np.int64)).to(dev)
+        for b in (5, 100, 2000):
+            ts = []
+            for rep in range(2):
+                h = rs.recsplit_build_u64(keys, leaf, b, stream.cuda_stream)
+                ts.append(rs.recsplit_last_profile()["ms_total"])
+                st = rs.recsplit_stats(h)
+                rs.recsplit_free(h)
+            rows.append({"leaf": leaf, "bucket": b, "n": n, "bits_per_key": st["bits_per_key"],
+                         "tree_bits_per_key": st["tree_bits_per_key"], "build_ms": min(ts),
+                         "keys_per_s": n / (min(ts) / 1e3)})
+    print(json.dumps({"metric": "space and construction time over (leaf, bucket)", "workload": "sweep",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -561,6 +594,8 @@ def main():
         return run_u64(a)
     if a.workload == "batch":
         return run_batch(a)
+    if a.workload == "sweep":
+        return run_sweep(a)
     return run_ours(a)
 
 

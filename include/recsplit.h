@@ -260,12 +260,16 @@ int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64
  *  leaf_chunk:   leaves a group takes from the work queue at a time (1..64)
  *  leaf_seeds_per_lane: indices each lane tests per round (1, 2, 4 or 8)
  *  split_warps[k]: warps per split node for levels whose largest node has
- *                <64 (k=0), <256 (k=1) or more (k=2) keys (1, 2, 4 or 8) */
+ *                <64 (k=0), <256 (k=1) or more (k=2) keys (1, 2, 4 or 8)
+ *  leaf_two_phase: 1 = test the first half of a leaf's keys for all of a
+ *                round's indices first and finish only the survivors (pays
+ *                for large leaves), 0 = test every index on all keys */
 typedef struct recsplit_tuning {
   uint32_t leaf_warps;
   uint32_t leaf_chunk;
   uint32_t leaf_seeds_per_lane;
   uint32_t split_warps[3];
+  uint32_t leaf_two_phase;
 } recsplit_tuning_t;
 
 /* Current launch shapes for leaf size l (process-wide). */

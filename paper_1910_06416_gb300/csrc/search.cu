@@ -340,7 +340,8 @@ __host__ __device__ constexpr int leaf_min_blocks(int l) { return l <= 5 ? 6 : (
 
 template <int LMAX, bool FULL>
 __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(SearchArgs a, uint32_t gwarps,
-                                                                            uint32_t chunk, uint32_t spl) {
+                                                                            uint32_t chunk, uint32_t spl,
+                                                                            uint32_t two_phase) {
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
   constexpr bool kTwoPhase = FULL && LMAX >= 4;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
           }
         }
         uint64_t found = ~0ull;
-        if (kTwoPhase) {
+        if (kTwoPhase && two_phase) {
           found = leaf_round_two_phase<LMAX>(x, base, depth, spl, lane, surv[warp]);
         } else {
           for (uint32_t j = 0; j < spl; j++) {
@@ -444,7 +445,7 @@ int launch_leaf_kernel(const SearchArgs& a, const recsplit_tuning_t& t, int sm_c
   int rc = persistent_grid(kern, 0, sm_count, &blocks);
   if (rc) return rc;
   RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
-  kern<<<blocks, kThreads, 0, s>>>(a, t.leaf_warps, t.leaf_chunk, t.leaf_seeds_per_lane);
+  kern<<<blocks, kThreads, 0, s>>>(a, t.leaf_warps, t.leaf_chunk, t.leaf_seeds_per_lane, t.leaf_two_phase);
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;
@@ -476,7 +477,8 @@ recsplit_tuning_t default_tuning(uint32_t leaf) {
   recsplit_tuning_t t;
   t.leaf_warps = leaf >= 12 ? 4 : 1;
   t.leaf_chunk = leaf >= 12 ? 1 : 4;
-  t.leaf_seeds_per_lane = leaf >= 4 ? 4 : 1;
+  t.leaf_two_phase = leaf >= 10 ? 1 : 0;
+  t.leaf_seeds_per_lane = t.leaf_two_phase ? 4 : 1;
   t.split_warps[0] = 1;
   t.split_warps[1] = leaf >= 12 ? 2 : 1;
   t.split_warps[2] = 8;

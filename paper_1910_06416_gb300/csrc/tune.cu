@@ -25,7 +25,7 @@ bool valid_tuning(const recsplit_tuning_t& t) {
     return false;
   for (uint32_t w : t.split_warps)
     if (!pow2_upto(w, 8)) return false;
-  return true;
+  return t.leaf_two_phase <= 1;
 }
 
 // Build of the sample under the installed shapes; leaf and split search
@@ -102,7 +102,17 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
   };
   do {
     if ((rc = measure(best, true, &leaf_ms))) break;
-    // leaf knobs, one at a time
+    // leaf knobs, one at a time: test mode (with its natural seeds per lane),
+    // warps, chunk, seeds per lane
+    for (uint32_t tp : {0u, 1u}) {
+      recsplit_tuning_t t = best;
+      t.leaf_two_phase = tp;
+      t.leaf_seeds_per_lane = tp ? 4 : 1;
+      double ms;
+      if ((rc = measure(t, true, &ms))) break;
+      if (ms < leaf_ms) leaf_ms = ms, best = t;
+    }
+    if (rc) break;
     for (uint32_t w : {1u, 2u, 4u, 8u}) {
       recsplit_tuning_t t = best;
       t.leaf_warps = w;

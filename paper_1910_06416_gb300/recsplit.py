@@ -64,12 +64,12 @@ class ServerStats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("leaf_warps", C.c_uint32), ("leaf_chunk", C.c_uint32), ("leaf_seeds_per_lane", C.c_uint32),
-                ("split_warps", C.c_uint32 * 3)]
+                ("split_warps", C.c_uint32 * 3), ("leaf_two_phase", C.c_uint32)]
 
 
 def _tuning_dict(t: Tuning) -> dict:
     return {"leaf_warps": t.leaf_warps, "leaf_chunk": t.leaf_chunk, "leaf_seeds_per_lane": t.leaf_seeds_per_lane,
-            "split_warps": list(t.split_warps)}
+            "split_warps": list(t.split_warps), "leaf_two_phase": t.leaf_two_phase}
 
 
 class RecSplitError(RuntimeError):
@@ -239,7 +239,7 @@ def recsplit_get_tuning(leaf_size: int) -> dict:
 
 def recsplit_set_tuning(leaf_size: int, tuning: dict) -> None:
     t = Tuning(tuning["leaf_warps"], tuning["leaf_chunk"], tuning["leaf_seeds_per_lane"],
-               (C.c_uint32 * 3)(*tuning["split_warps"]))
+               (C.c_uint32 * 3)(*tuning["split_warps"]), tuning.get("leaf_two_phase", 0))
     _check(lib().recsplit_set_tuning(leaf_size, C.byref(t)), "recsplit_set_tuning")
 
 

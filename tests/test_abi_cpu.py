@@ -65,7 +65,7 @@ def test_tuning_shapes_are_validated(rs):
     t = rs.recsplit_get_tuning(8)
     assert t["leaf_warps"] in (1, 2, 4, 8)
     for bad in ({"leaf_warps": 3}, {"leaf_chunk": 0}, {"leaf_chunk": 65}, {"leaf_seeds_per_lane": 16},
-                {"split_warps": [1, 16, 8]}):
+                {"split_warps": [1, 16, 8]}, {"leaf_two_phase": 2}):
         tt = dict(t, **bad)
         with pytest.raises(rs.RecSplitError) as e:
             rs.recsplit_set_tuning(8, tt)

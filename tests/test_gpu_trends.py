@@ -1,0 +1,48 @@
+"""The paper's qualitative claims on the GPU path (Sec. 8): larger leaves give
+smaller structures, and construction time grows by about e per unit of leaf
+size; bits per key barely depend on the number of keys."""
+import numpy as np
+import pytest
+
+from paper_1910_06416_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1910_06416_gb300 import build
+    build.build()
+    import paper_1910_06416_gb300.recsplit as rs
+    rs.lib()
+    return rs
+
+
+def test_leaf_size_trends(rs):
+    keys = torch.from_numpy(inputs.u64_keys(300_000, 4).view(np.int64)).cuda()
+    rs.recsplit_set_profiling(True)
+    bits, work = {}, {}
+    for leaf in range(6, 14):
+        h = rs.recsplit_build_u64(keys, leaf, 100)
+        bits[leaf] = rs.recsplit_stats(h)["bits_per_key"]
+        p = rs.recsplit_last_profile()
+        work[leaf] = p["leaf_evals"] + p["split_evals"]
+        rs.recsplit_free(h)
+    rs.recsplit_set_profiling(False)
+    assert all(bits[l + 1] < bits[l] + 0.02 for l in range(6, 13))
+    assert bits[13] < bits[6] - 0.2
+    # search work per unit of leaf size: about e (the paper plots time)
+    ratios = [work[l + 1] / work[l] for l in range(8, 13)]
+    assert all(1.8 < r < 4.0 for r in ratios), ratios
+
+
+def test_bits_per_key_independent_of_n(rs):
+    out = []
+    for n in (100_000, 1_000_000, 10_000_000):
+        h = rs.recsplit_build_u64(torch.from_numpy(inputs.u64_keys(n, 8).view(np.int64)).cuda(), 8, 100)
+        out.append(rs.recsplit_stats(h)["bits_per_key"])
+        rs.recsplit_free(h)
+    assert max(out) - min(out) < 0.03, out

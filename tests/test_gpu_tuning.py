@@ -21,9 +21,10 @@ def rs():
 
 
 SHAPES = [
-    {"leaf_warps": 1, "leaf_chunk": 1, "leaf_seeds_per_lane": 1, "split_warps": [1, 1, 1]},
-    {"leaf_warps": 8, "leaf_chunk": 64, "leaf_seeds_per_lane": 8, "split_warps": [8, 8, 8]},
-    {"leaf_warps": 2, "leaf_chunk": 16, "leaf_seeds_per_lane": 2, "split_warps": [2, 4, 2]},
+    {"leaf_warps": 1, "leaf_chunk": 1, "leaf_seeds_per_lane": 1, "split_warps": [1, 1, 1], "leaf_two_phase": 0},
+    {"leaf_warps": 8, "leaf_chunk": 64, "leaf_seeds_per_lane": 8, "split_warps": [8, 8, 8], "leaf_two_phase": 1},
+    {"leaf_warps": 2, "leaf_chunk": 16, "leaf_seeds_per_lane": 2, "split_warps": [2, 4, 2], "leaf_two_phase": 1},
+    {"leaf_warps": 4, "leaf_chunk": 4, "leaf_seeds_per_lane": 1, "split_warps": [1, 2, 8], "leaf_two_phase": 1},
 ]
 
 
