@@ -95,12 +95,16 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
   auto measure = [&](const recsplit_tuning_t& t, bool leaf_phase, double* ms) -> int {
     set_tuning_for(leaf_size, t);
     double l, sp;
-    int r = time_build(in, s, 2, &l, &sp);
+    int r = time_build(in, s, 3, &l, &sp);
     if (r) return r;
     *ms = leaf_phase ? l : sp;
     return RECSPLIT_OK;
   };
+  // a candidate replaces the current shape only if clearly faster (timing noise)
+  auto better = [](double cand, double cur) { return cand < 0.97 * cur; };
   do {
+    double warm;
+    if ((rc = measure(best, true, &warm))) break;  // first builds grow the memory pool: discarded
     if ((rc = measure(best, true, &leaf_ms))) break;
     // leaf knobs, one at a time: test mode (with its natural seeds per lane),
     // warps, chunk, seeds per lane
@@ -110,7 +114,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
       t.leaf_seeds_per_lane = tp ? 4 : 1;
       double ms;
       if ((rc = measure(t, true, &ms))) break;
-      if (ms < leaf_ms) leaf_ms = ms, best = t;
+      if (better(ms, leaf_ms)) leaf_ms = ms, best = t;
     }
     if (rc) break;
     for (uint32_t w : {1u, 2u, 4u, 8u}) {
@@ -118,7 +122,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
       t.leaf_warps = w;
       double ms;
       if ((rc = measure(t, true, &ms))) break;
-      if (ms < leaf_ms) leaf_ms = ms, best = t;
+      if (better(ms, leaf_ms)) leaf_ms = ms, best = t;
     }
     if (rc) break;
     for (uint32_t c : {1u, 4u, 16u}) {
@@ -126,7 +130,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
       t.leaf_chunk = c;
       double ms;
       if ((rc = measure(t, true, &ms))) break;
-      if (ms < leaf_ms) leaf_ms = ms, best = t;
+      if (better(ms, leaf_ms)) leaf_ms = ms, best = t;
     }
     if (rc) break;
     for (uint32_t k : {1u, 2u, 4u, 8u}) {
@@ -134,7 +138,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
       t.leaf_seeds_per_lane = k;
       double ms;
       if ((rc = measure(t, true, &ms))) break;
-      if (ms < leaf_ms) leaf_ms = ms, best = t;
+      if (better(ms, leaf_ms)) leaf_ms = ms, best = t;
     }
     if (rc) break;
     // split knobs per node-size class
@@ -145,7 +149,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
         t.split_warps[cls] = w;
         double ms;
         if ((rc = measure(t, false, &ms))) break;
-        if (ms < split_ms) split_ms = ms, best = t;
+        if (better(ms, split_ms)) split_ms = ms, best = t;
       }
     }
   } while (false);
