@@ -147,7 +147,7 @@ __global__ void k_bucket_codes(const uint64_t* __restrict__ counts, const uint32
                                const DevSet* __restrict__ sets, uint64_t nbt, ClassTables ct,
                                uint64_t* __restrict__ codes) {
   for (uint64_t b = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; b < nbt; b += uint64_t(gridDim.x) * blockDim.x)
-    codes[b] = ct.t[sets[bset[b]].cls][kTableWords * counts[b] + kTabSkip] >> 32;
+    codes[b] = ct.t[sets[bset[b]].cls][kTableWords * counts[b]] >> 32;
 }
 
 // Sec. 9: grouping by bucket; the order inside a bucket does not matter
@@ -194,11 +194,11 @@ __global__ void k_bucket_bits(const uint64_t* __restrict__ counts, const uint64_
     const uint32_t cls = sets[bset[b]].cls;
     const uint64_t* table = ct.t[cls];
     const uint64_t m = counts[b];
-    uint64_t len = static_cast<uint32_t>(table[kTableWords * m + kTabSkip]);
+    uint64_t len = static_cast<uint32_t>(table[kTableWords * m]);
     if (!failed) {
       for (uint64_t c = cbase[b], e = cbase[b + 1]; c < e; c++) {
         const uint32_t sz = sizes[c];
-        const uint32_t r = sz <= ct.mmax[cls] ? static_cast<uint32_t>(table[kTableWords * sz + kTabShape] >> 40) & 31 : 0;
+        const uint32_t r = sz <= ct.mmax[cls] ? static_cast<uint32_t>(table[kTableWords * sz + 1] >> 40) & 31 : 0;
         len += (seeds[c] >> r) + 1;
       }
     }
@@ -306,12 +306,12 @@ __global__ void k_write_codes(const uint64_t* __restrict__ counts, const uint64_
     uint64_t* tree = outs[si].tree;
     const uint64_t base = off[b] - off[sets[si].bucket_base];
     uint64_t fpos = base;
-    uint64_t upos = base + static_cast<uint32_t>(table[kTableWords * m + kTabSkip]);
+    uint64_t upos = base + static_cast<uint32_t>(table[kTableWords * m]);
     BitSink fixed{tree}, unary{tree};
     const uint64_t mmax = ct.mmax[sets[si].cls];
     for (uint64_t c = cbase[b], e = cbase[b + 1]; c < e; c++) {
       const uint32_t sz = sizes[c];
-      const uint32_t r = sz <= mmax ? static_cast<uint32_t>(table[kTableWords * sz + kTabShape] >> 40) & 31 : 0;
+      const uint32_t r = sz <= mmax ? static_cast<uint32_t>(table[kTableWords * sz + 1] >> 40) & 31 : 0;
       const uint64_t s = seeds[c];
       fixed.put(fpos, r ? (s & ((1ull << r) - 1)) : 0, r);
       fpos += r;

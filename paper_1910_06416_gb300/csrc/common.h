@@ -56,13 +56,11 @@ Shape shape_of(const Strategy& st, uint64_t m);
 int golomb_rice_param(const Strategy& st, uint64_t m);
 
 // Per-size tables for node sizes 0 .. mmax.  Device form: four words per size
-//   kTabShape  = unit | fanout << 32 | r << 40
-//   kTabMagic  = ceil(2^32 / unit) for unit >= 2 (exact floor(v / unit) for v < m < 2^16), else 0
-//   kTabSkip   = fixed_bits(subtree) | codes(subtree) << 32
-//   kTabTrials = expected number of trials (1/p rounded up)
-// (shape and magic are adjacent: one 16-byte load in the lookup descent)
+//   w0 = fixed_bits(subtree) | codes(subtree) << 32
+//   w1 = unit | fanout << 32 | r << 40
+//   w2 = expected number of trials (1/p rounded up)
+//   w3 = ceil(2^32 / unit) for unit >= 2 (exact floor(v / unit) for v < m < 2^16), else 0
 constexpr int kTableWords = 4;
-constexpr int kTabShape = 0, kTabMagic = 1, kTabSkip = 2, kTabTrials = 3;
 struct Tables {
   uint64_t mmax = 0;
   std::vector<uint8_t> r;

@@ -124,35 +124,18 @@ __device__ __forceinline__ uint32_t select_in_word(uint64_t word, uint32_t k) {
   return pos;
 }
 
-// Position of the one of rank `rank` (0-based) counting from position `pos`
-// (the first one at or after pos has rank 0).  After the first word the scan
-// moves by 16-byte aligned pairs of words (one 128-bit load per pair); every
-// bit array here is followed by another section of the same structure, so the
-// second word of the last pair is always inside the allocation.
+// Position of the one of rank `rank` (0-based) counting from the one at
+// position `pos` (rank 0), scanning words.
 __device__ __forceinline__ uint64_t select_from(const uint64_t* a, uint64_t pos, uint64_t rank) {
   uint64_t w = pos >> 6;
   uint64_t word = __ldg(a + w) & (~0ull << (pos & 63));
-  uint32_t c = __popcll(word);
-  if (rank < c) return (w << 6) + select_in_word(word, static_cast<uint32_t>(rank));
-  rank -= c;
-  w++;
-  if (reinterpret_cast<uintptr_t>(a + w) & 15) {  // reach a 16-byte boundary
-    word = __ldg(a + w);
-    c = __popcll(word);
-    if (rank < c) return (w << 6) + select_in_word(word, static_cast<uint32_t>(rank));
-    rank -= c;
-    w++;
-  }
   for (;;) {
-    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(a + w));
-    const uint32_t c0 = __popcll(v.x);
-    if (rank < c0) return (w << 6) + select_in_word(v.x, static_cast<uint32_t>(rank));
-    rank -= c0;
-    const uint32_t c1 = __popcll(v.y);
-    if (rank < c1) return ((w + 1) << 6) + select_in_word(v.y, static_cast<uint32_t>(rank));
-    rank -= c1;
-    w += 2;
+    const uint32_t c = __popcll(word);
+    if (rank < c) break;
+    rank -= c;
+    word = __ldg(a + (++w));
   }
+  return (w << 6) + select_in_word(word, static_cast<uint32_t>(rank));
 }
 
 // Position of the first one at or after `pos`.

@@ -30,12 +30,11 @@ __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint6
   const uint64_t o = static_cast<uint64_t>(z + static_cast<int64_t>(bs));
 
   uint64_t fixed = o;
-  uint64_t unary = o + static_cast<uint32_t>(__ldg(v.table + kTableWords * m + kTabSkip));
+  uint64_t unary = o + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
   uint64_t c = 0;
   const uint64_t xpre = pre_key(lo);
   for (uint32_t depth = 0;; depth++) {
-    const ulonglong2 sm = __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * m));
-    const uint64_t w1 = sm.x;  // shape; sm.y = reciprocal of the unit
+    const uint64_t w1 = __ldg(v.table + kTableWords * m + 1);
     const uint32_t r = static_cast<uint32_t>(w1 >> 40) & 31;
     const uint32_t fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
     const uint32_t unit = static_cast<uint32_t>(w1);
@@ -46,10 +45,10 @@ __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint6
     unary = one + 1;
     const uint32_t val = phi_pre(xpre, family_key(seed, depth), m);
     if (fanout == 0) return s0 + c + val;
-    const uint32_t magic = static_cast<uint32_t>(sm.y);
+    const uint32_t magic = static_cast<uint32_t>(__ldg(v.table + kTableWords * m + 3));
     const uint32_t part = min(magic && m < 65536 ? __umulhi(val, magic) : val / unit, fanout - 1);
     if (part) {
-      const uint64_t wu = __ldg(v.table + kTableWords * unit + kTabSkip);
+      const uint64_t wu = __ldg(v.table + kTableWords * unit);
       fixed += uint64_t(part) * static_cast<uint32_t>(wu);
       const uint64_t skip = uint64_t(part) * (wu >> 32);
       if (skip) unary = select_from(v.tree, unary, skip - 1) + 1;

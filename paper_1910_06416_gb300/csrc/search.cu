@@ -51,7 +51,7 @@ __device__ __forceinline__ uint64_t volatile_load(const uint64_t* p) {
 // number of trials (probability about e^-64) is checked for keys that can
 // never be separated.
 __device__ __forceinline__ uint64_t stall_threshold(const uint64_t* table, uint32_t m) {
-  const uint64_t e = table[kTableWords * m + kTabTrials];
+  const uint64_t e = table[kTableWords * m + 2];
   return e > (kMaxTrials >> 6) ? kMaxTrials : e << 6;
 }
 
@@ -60,7 +60,7 @@ __device__ __forceinline__ uint64_t stall_threshold(const uint64_t* table, uint3
 // probability below e^-1024; the limit bounds the time of a search that can
 // never succeed.
 __device__ __forceinline__ uint64_t trial_limit(const uint64_t* table, uint32_t m) {
-  const uint64_t e = table[kTableWords * m + kTabTrials];
+  const uint64_t e = table[kTableWords * m + 2];
   if (e > (kMaxTrials >> 10)) return kMaxTrials;
   return max(uint64_t(4096), e << 10);
 }
@@ -166,7 +166,7 @@ __device__ void emit_children(const SearchArgs& a, const Node& nd, const uint64_
   const bool valid = t < fanout && k >= 2;
   const uint32_t kind = k == leaf ? 0 : (k < leaf ? 1 : 2);
   const uint32_t c_of_node = nd.depth >> 8;
-  const uint32_t unit_codes = static_cast<uint32_t>(table[kTableWords * unit + kTabSkip] >> 32);
+  const uint32_t unit_codes = static_cast<uint32_t>(table[kTableWords * unit] >> 32);
   Node child;
   child.start = nd.start + t * unit;
   child.m = k;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     const Node nd = a.split_in[idx];
     const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
     const uint64_t* table = a.table[cls];
-    const uint64_t w1 = table[kTableWords * nd.m + kTabShape];
+    const uint64_t w1 = table[kTableWords * nd.m + 1];
     SplitParams sp;
     sp.m = nd.m;
     sp.unit = static_cast<uint32_t>(w1);

@@ -109,11 +109,11 @@ int build_tables(uint32_t leaf, uint64_t mmax, Tables* T, std::string* err) {
       if (err) *err = "node size too large for the device tables";
       return RECSPLIT_E_INVALID;
     }
-    T->device_words[kTableWords * m + kTabSkip] = fb | (nc << 32);
-    T->device_words[kTableWords * m + kTabShape] =
+    T->device_words[kTableWords * m] = fb | (nc << 32);
+    T->device_words[kTableWords * m + 1] =
         sh.unit | (static_cast<uint64_t>(sh.fanout) << 32) | (static_cast<uint64_t>(r) << 40);
-    T->device_words[kTableWords * m + kTabTrials] = T->expected_trials[m];
-    T->device_words[kTableWords * m + kTabMagic] = sh.unit >= 2 ? ((1ull << 32) + sh.unit - 1) / sh.unit : 0;
+    T->device_words[kTableWords * m + 2] = T->expected_trials[m];
+    T->device_words[kTableWords * m + 3] = sh.unit >= 2 ? ((1ull << 32) + sh.unit - 1) / sh.unit : 0;
   }
   // sizes 0 and 1: leaves without a code
   return RECSPLIT_OK;
