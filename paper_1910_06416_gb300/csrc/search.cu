@@ -336,15 +336,14 @@ __device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const
 }
 
 // Blocks per SM the register budget must allow (keys live in registers).
-__host__ __device__ constexpr int leaf_min_blocks(int l) { return l <= 5 ? 6 : (l <= 8 ? 5 : (l <= 16 ? 4 : 3)); }
+__host__ __device__ constexpr int leaf_min_blocks(int l) { return l <= 5 ? 5 : (l <= 12 ? 4 : 3); }
 
-template <int LMAX, bool FULL>
+template <int LMAX, bool FULL, bool TWO>
 __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(SearchArgs a, uint32_t gwarps,
-                                                                            uint32_t chunk, uint32_t spl,
-                                                                            uint32_t two_phase) {
+                                                                            uint32_t chunk, uint32_t spl) {
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
-  constexpr bool kTwoPhase = FULL && LMAX >= 4;
+  constexpr bool kTwoPhase = FULL && TWO && LMAX >= 4;
   __shared__ uint2 surv[kTwoPhase ? kWarps : 1][kTwoPhase ? 32 * kMaxSpl : 1];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t gid = warp / gwarps, wig = warp % gwarps;
@@ -404,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
           }
         }
         uint64_t found = ~0ull;
-        if (kTwoPhase && two_phase) {
+        if (kTwoPhase) {
           found = leaf_round_two_phase<LMAX>(x, base, depth, spl, lane, surv[warp]);
         } else {
           for (uint32_t j = 0; j < spl; j++) {
@@ -438,14 +437,14 @@ int persistent_grid(K kernel, size_t smem, int sm_count, int* blocks) {
   return RECSPLIT_OK;
 }
 
-template <int LMAX, bool FULL>
+template <int LMAX, bool FULL, bool TWO = false>
 int launch_leaf_kernel(const SearchArgs& a, const recsplit_tuning_t& t, int sm_count, cudaStream_t s) {
-  auto kern = k_leaves<LMAX, FULL>;
+  auto kern = k_leaves<LMAX, FULL, TWO>;
   int blocks = 0;
   int rc = persistent_grid(kern, 0, sm_count, &blocks);
   if (rc) return rc;
   RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
-  kern<<<blocks, kThreads, 0, s>>>(a, t.leaf_warps, t.leaf_chunk, t.leaf_seeds_per_lane, t.leaf_two_phase);
+  kern<<<blocks, kThreads, 0, s>>>(a, t.leaf_warps, t.leaf_chunk, t.leaf_seeds_per_lane);
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;
@@ -453,7 +452,8 @@ int launch_leaf_kernel(const SearchArgs& a, const recsplit_tuning_t& t, int sm_c
 
 template <int L>
 int launch_full(const SearchArgs& a, const recsplit_tuning_t& t, int sm, cudaStream_t s) {
-  return launch_leaf_kernel<L, true>(a, t, sm, s);
+  if (t.leaf_two_phase) return launch_leaf_kernel<L, true, true>(a, t, sm, s);
+  return launch_leaf_kernel<L, true, false>(a, t, sm, s);
 }
 
 typedef int (*FullLauncher)(const SearchArgs&, const recsplit_tuning_t&, int, cudaStream_t);
