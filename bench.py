@@ -58,6 +58,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    rank's times); the identity outside torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -326,12 +338,7 @@ def run_ours(a):
     build_ms = [ev[0].elapsed_time(ev[1]) for _, ev, _ in records]
     look_ms = [ev[1].elapsed_time(ev[2]) for _, ev, _ in records]
     profs = [p for _, _, p in records]
-    if world > 1:
-        t = torch.tensor([total_ms, sum(build_ms), sum(look_ms)], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, sb, sl = (float(x) for x in t.tolist())
-    else:
-        sb, sl = sum(build_ms), sum(look_ms)
+    total_ms, sb, sl = max_over_ranks([total_ms, sum(build_ms), sum(look_ms)], dev)
     value = world * a.n * a.steps / (sb / 1000.0)
     lookup_qps = world * a.queries * a.steps / (sl / 1000.0)
 

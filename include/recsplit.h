@@ -44,6 +44,7 @@ extern "C" {
 #define RECSPLIT_E_SEARCH_LIMIT (-4) /* a split or bijection search passed 2^36 trials */
 #define RECSPLIT_E_NOMEM (-5)        /* device or host allocation failed */
 #define RECSPLIT_E_CUDA (-6)         /* a CUDA runtime call failed */
+#define RECSPLIT_E_TIMEOUT (-7)      /* the build did not finish within the calling thread's time limit */
 
 /* Opaque handle to a built structure resident in device memory. */
 typedef struct recsplit recsplit_t;
@@ -282,6 +283,19 @@ int recsplit_set_tuning(uint32_t leaf_size, const recsplit_tuning_t* t);
  * and returns them in *out (may be NULL).  Uses the current device. */
 int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_keys, void* stream,
                       recsplit_tuning_t* out);
+
+/* Time limit in milliseconds for builds on the calling host thread (0 = none,
+ * the default).  A build that has not finished when the limit passes is
+ * cancelled: the host sets the build's device error word, the search kernels
+ * see it within 256 rounds of any search and stop, and the call returns
+ * RECSPLIT_E_TIMEOUT once the device work has drained.  The device stays
+ * usable. */
+int recsplit_set_timeout_ms(uint32_t ms);
+
+/* Fault injection for tests of the error paths (host side only): the
+ * (after + 1)-th device allocation of the library on the calling host thread
+ * fails as if the device were out of memory; after < 0 disarms. */
+int recsplit_inject_alloc_failure(int64_t after);
 
 /* Golomb-Rice parameters of nodes of 0 .. m_hi keys for leaf size l
  * (Sec. 5.4 Eq. gr with the probabilities of Sec. 5.1 / 5.2, and the integer

@@ -1,7 +1,9 @@
 // C ABI entry points (include/recsplit.h): argument checks, host/device
 // buffer staging, serialization and error reporting.
+#include <chrono>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -47,7 +49,16 @@ int device_pool(cudaMemPool_t* pool) {
   return RECSPLIT_OK;
 }
 
+static thread_local int64_t g_fail_alloc_after = -1;
+static thread_local uint32_t g_timeout_ms = 0;
+
+uint32_t timeout_ms() { return g_timeout_ms; }
+
 int pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  if (g_fail_alloc_after >= 0 && g_fail_alloc_after-- == 0) {
+    *p = nullptr;
+    return fail(RECSPLIT_E_NOMEM, "device allocation failed (injected)");
+  }
   cudaMemPool_t pool;
   int rc = device_pool(&pool);
   if (rc) return rc;
@@ -56,6 +67,43 @@ int pool_alloc(void** p, size_t bytes, cudaStream_t s) {
     return fail(RECSPLIT_E_NOMEM, "device allocation failed");
   }
   return RECSPLIT_OK;
+}
+
+int wait_stream(cudaStream_t s, int* d_error, uint32_t ms) {
+  if (ms == 0) {
+    RS_CUDA(cudaStreamSynchronize(s));
+    return RECSPLIT_OK;
+  }
+  cudaEvent_t ev;
+  RS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, s);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_fail(e, "event record");
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  bool cancelled = false;
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      cudaEventDestroy(ev);
+      return cuda_fail(e, "waiting for the build");
+    }
+    if (!cancelled && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(ms)) {
+      cancelled = true;
+      static const int code = RECSPLIT_E_TIMEOUT;
+      cudaStream_t side;
+      if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess) {
+        cudaMemcpyAsync(d_error, &code, sizeof(int), cudaMemcpyHostToDevice, side);
+        cudaStreamSynchronize(side);
+        cudaStreamDestroy(side);
+      }
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  return cancelled ? fail(RECSPLIT_E_TIMEOUT, "build cancelled after its time limit") : RECSPLIT_OK;
 }
 
 static thread_local bool g_profiling = false;
@@ -397,6 +445,7 @@ const char* recsplit_strerror(int code) {
     case RECSPLIT_E_SEARCH_LIMIT: return "seed search limit reached";
     case RECSPLIT_E_NOMEM: return "out of memory";
     case RECSPLIT_E_CUDA: return "CUDA runtime error";
+    case RECSPLIT_E_TIMEOUT: return "time limit passed";
     default: return "unknown error";
   }
 }
@@ -416,5 +465,15 @@ int recsplit_last_profile(recsplit_profile_t* out) {
 }
 
 uint64_t recsplit_launch_count(void) { return g_launches; }
+
+int recsplit_set_timeout_ms(uint32_t ms) {
+  g_timeout_ms = ms;
+  return RECSPLIT_OK;
+}
+
+int recsplit_inject_alloc_failure(int64_t after) {
+  g_fail_alloc_after = after < 0 ? -1 : after;
+  return RECSPLIT_OK;
+}
 
 }  // extern "C"

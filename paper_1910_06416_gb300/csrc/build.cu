@@ -755,7 +755,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   RS_CUDA(cudaMemcpyAsync(h_codes.data(), set_codes, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_db.data(), set_db, count * sizeof(long long), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(&herr, d_error, sizeof(int), cudaMemcpyDeviceToHost, s));
-  RS_CUDA(cudaStreamSynchronize(s));
+  if ((rc = wait_stream(s, d_error, timeout_ms()))) return rc;
   if (herr == RECSPLIT_E_DUPLICATE) return fail(herr, "two keys share their lower signature half (duplicate keys)");
   if (herr == RECSPLIT_E_SEARCH_LIMIT) return fail(herr, "seed search exceeded its limit");
   if (herr) return fail(herr, "internal consistency check failed during the search");

@@ -112,6 +112,13 @@ View make_view(const Handle& h);
 int device_pool(cudaMemPool_t* pool);
 int pool_alloc(void** p, size_t bytes, cudaStream_t s);
 
+// Waits for the work queued on s so far.  With a time limit (ms > 0) the wait
+// polls; past the limit it writes RECSPLIT_E_TIMEOUT into *d_error (the
+// searches poll it and stop), waits for the queue to drain and returns
+// RECSPLIT_E_TIMEOUT.
+int wait_stream(cudaStream_t s, int* d_error, uint32_t ms);
+uint32_t timeout_ms();
+
 // ---------------------------------------------------------------- tracing
 bool profiling_enabled();
 void store_profile(const recsplit_profile_t& p);

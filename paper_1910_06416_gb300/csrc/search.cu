@@ -117,8 +117,11 @@ __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ k
                                                   uint64_t* best, uint64_t stall, uint64_t limit,
                                                   int* err) {
   bool checked = false;
+  uint32_t rounds = 0;
   for (uint64_t base = uint64_t(wig) * 32;; base += uint64_t(gwarps) * 32) {
     if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(best))) break;
+    if ((++rounds & 255) == 0 && __shfl_sync(0xFFFFFFFFu, lane == 0 ? *reinterpret_cast<volatile int*>(err) : 0, 0))
+      break;  // another search failed, or the host cancelled the build
     if (base >= limit) {
       if (lane == 0) {
         set_error(err, RECSPLIT_E_SEARCH_LIMIT);
@@ -375,11 +378,15 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
       const uint64_t stall = stall_threshold(table, m);
       const uint64_t limit = trial_limit(table, m);
       bool checked = false;
+      uint32_t rounds = 0;
       // a round of a warp covers the spl * 32 indices from base; lane L tests
       // base + j * 32 + L for j < spl
       const uint64_t span = uint64_t(spl) * 32;
       for (uint64_t base = uint64_t(wig) * span;; base += uint64_t(gwarps) * span) {
         if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(&best[gid]))) break;
+        if ((++rounds & 255) == 0 &&
+            __shfl_sync(0xFFFFFFFFu, lane == 0 ? *reinterpret_cast<volatile int*>(a.error) : 0, 0))
+          break;  // another search failed, or the host cancelled the build
         if (base >= limit) {
           if (lane == 0) {
             set_error(a.error, RECSPLIT_E_SEARCH_LIMIT);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "librecsplit.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "recsplit.h")
 
 OK = 0
-E_INVALID, E_DUPLICATE, E_SEARCH_LIMIT, E_NOMEM, E_CUDA = -1, -2, -4, -5, -6
+E_INVALID, E_DUPLICATE, E_SEARCH_LIMIT, E_NOMEM, E_CUDA, E_TIMEOUT = -1, -2, -4, -5, -6, -7
 
 _lock = threading.Lock()
 _lib = None
@@ -111,6 +111,8 @@ def lib():
             L.recsplit_lookup_u64_static.argtypes = [p, p, u64, p, p]
             L.recsplit_build_batch.argtypes = [p, u32, p, p]
             L.recsplit_get_tuning.argtypes = [u32, p]
+            L.recsplit_set_timeout_ms.argtypes = [u32]
+            L.recsplit_inject_alloc_failure.argtypes = [C.c_int64]
             L.recsplit_set_tuning.argtypes = [u32, p]
             L.recsplit_autotune.argtypes = [u32, u32, u64, p, p]
             L.recsplit_server_create.argtypes = [p, p]
@@ -135,7 +137,8 @@ def lib():
                          "recsplit_server_submit_build_bytes", "recsplit_server_submit_lookup_u64",
                          "recsplit_server_submit_lookup_bytes", "recsplit_server_poll", "recsplit_server_structure",
                          "recsplit_server_release", "recsplit_server_stats",
-                         "recsplit_get_tuning", "recsplit_set_tuning", "recsplit_autotune"):
+                         "recsplit_get_tuning", "recsplit_set_tuning", "recsplit_autotune",
+                         "recsplit_set_timeout_ms", "recsplit_inject_alloc_failure"):
                 getattr(L, name).restype = i
             _lib = L
     return _lib
@@ -228,6 +231,15 @@ def recsplit_lookup_batch(handles, ids, keys, out, stream=None) -> None:
     hs = (C.c_void_p * max(1, len(handles)))(*handles)
     _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _ptr(ids), _ptr(keys), _count(keys),
                                        _ptr(out), _stream(stream)), "recsplit_lookup_batch")
+
+
+# ---------------------------------------------------------------- failures
+def recsplit_set_timeout_ms(ms: int) -> None:
+    _check(lib().recsplit_set_timeout_ms(ms), "recsplit_set_timeout_ms")
+
+
+def recsplit_inject_alloc_failure(after: int) -> None:
+    _check(lib().recsplit_inject_alloc_failure(after), "recsplit_inject_alloc_failure")
 
 
 # ---------------------------------------------------------------- tuning
