@@ -751,11 +751,14 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   std::vector<long long> h_db(count);
   std::vector<uint64_t> h_T(count), h_codes(count);
   int herr = 0;
+  // the deadline wait comes first: a copy into pageable host memory would
+  // itself wait for the whole search
+  if ((rc = wait_stream(s, d_error, timeout_ms()))) return rc;
   RS_CUDA(cudaMemcpyAsync(h_T.data(), set_T, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_codes.data(), set_codes, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_db.data(), set_db, count * sizeof(long long), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(&herr, d_error, sizeof(int), cudaMemcpyDeviceToHost, s));
-  if ((rc = wait_stream(s, d_error, timeout_ms()))) return rc;
+  RS_CUDA(cudaStreamSynchronize(s));
   if (herr == RECSPLIT_E_DUPLICATE) return fail(herr, "two keys share their lower signature half (duplicate keys)");
   if (herr == RECSPLIT_E_SEARCH_LIMIT) return fail(herr, "seed search exceeded its limit");
   if (herr) return fail(herr, "internal consistency check failed during the search");
