@@ -69,7 +69,11 @@ int pool_alloc(void** p, size_t bytes, cudaStream_t s) {
   return RECSPLIT_OK;
 }
 
-int wait_stream(cudaStream_t s, int* d_error, uint32_t ms) {
+double steady_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int wait_stream(cudaStream_t s, int* d_error, uint32_t ms, double start_ms) {
   if (ms == 0) {
     RS_CUDA(cudaStreamSynchronize(s));
     return RECSPLIT_OK;
@@ -81,7 +85,6 @@ int wait_stream(cudaStream_t s, int* d_error, uint32_t ms) {
     cudaEventDestroy(ev);
     return cuda_fail(e, "event record");
   }
-  const auto t0 = std::chrono::steady_clock::now();
   bool cancelled = false;
   for (;;) {
     e = cudaEventQuery(ev);
@@ -90,7 +93,7 @@ int wait_stream(cudaStream_t s, int* d_error, uint32_t ms) {
       cudaEventDestroy(ev);
       return cuda_fail(e, "waiting for the build");
     }
-    if (!cancelled && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(ms)) {
+    if (!cancelled && steady_ms() - start_ms > ms) {
       cancelled = true;
       static const int code = RECSPLIT_E_TIMEOUT;
       cudaStream_t side;

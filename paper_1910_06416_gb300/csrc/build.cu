@@ -472,6 +472,7 @@ uint64_t tiles(uint64_t items) { return (items + kTile - 1) / kTile; }
 int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cudaStream_t s, Handle** out) {
   for (uint32_t i = 0; i < count; i++) out[i] = nullptr;
   if (count == 0) return RECSPLIT_OK;
+  const double t_call = steady_ms();
   int dev = 0, sm_count = 0;
   RS_CUDA(cudaGetDevice(&dev));
   RS_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -753,7 +754,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   int herr = 0;
   // the deadline wait comes first: a copy into pageable host memory would
   // itself wait for the whole search
-  if ((rc = wait_stream(s, d_error, timeout_ms()))) return rc;
+  if ((rc = wait_stream(s, d_error, timeout_ms(), t_call))) return rc;
   RS_CUDA(cudaMemcpyAsync(h_T.data(), set_T, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_codes.data(), set_codes, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_db.data(), set_db, count * sizeof(long long), cudaMemcpyDeviceToHost, s));

@@ -112,12 +112,13 @@ View make_view(const Handle& h);
 int device_pool(cudaMemPool_t* pool);
 int pool_alloc(void** p, size_t bytes, cudaStream_t s);
 
-// Waits for the work queued on s so far.  With a time limit (ms > 0) the wait
-// polls; past the limit it writes RECSPLIT_E_TIMEOUT into *d_error (the
-// searches poll it and stop), waits for the queue to drain and returns
-// RECSPLIT_E_TIMEOUT.
-int wait_stream(cudaStream_t s, int* d_error, uint32_t ms);
+// Waits for the work queued on s so far.  With a time limit (ms > 0, counted
+// from `start_ms`, a steady-clock time in ms) the wait polls; past the limit it
+// writes RECSPLIT_E_TIMEOUT into *d_error (the searches poll it and stop),
+// waits for the queue to drain and returns RECSPLIT_E_TIMEOUT.
+int wait_stream(cudaStream_t s, int* d_error, uint32_t ms, double start_ms);
 uint32_t timeout_ms();
+double steady_ms();
 
 // ---------------------------------------------------------------- tracing
 bool profiling_enabled();

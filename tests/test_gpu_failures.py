@@ -26,6 +26,8 @@ def rs():
 
 def test_time_limit_cancels_a_long_build(rs, orc):
     keys = torch.from_numpy(inputs.u64_keys(300_000, 2).view(np.int64)).cuda()  # ~0.3 s at l=16, b=2000
+    # load the l = 16 kernels first (their first launch loads them, which blocks the host)
+    rs.recsplit_free(rs.recsplit_build_u64(keys[:3000], 16, 2000))
     rs.recsplit_set_timeout_ms(20)
     try:
         t0 = time.time()
