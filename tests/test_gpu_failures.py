@@ -62,8 +62,8 @@ def test_injected_allocation_failures(rs, orc):
             s = rs.Structure.build_u64(keys, 8, 100)  # host keys: staging allocation too
             assert np.array_equal(s.serialize(), ref)
             break
-        except rs.RecSplitError as e:
-            assert e.value.code == rs.E_NOMEM
+        except rs.RecSplitError as err:
+            assert err.code == rs.E_NOMEM
             failures += 1
         finally:
             rs.recsplit_inject_alloc_failure(-1)
