@@ -166,7 +166,8 @@ struct BuildOptions {
 // Builds one structure per set in one pass over all sets (out[i] for set i).
 // KeyInput pointers must be device memory.
 int build_sets(const SetInput* sets, uint32_t count, const BuildOptions& opt, cudaStream_t s, Handle** out);
-int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s);
+// allow_scratch = false: allocate nothing (no per-batch decode of the lists)
+int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s, bool allow_scratch = true);
 int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
                 cudaStream_t s);
 int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t* d_bytes, const uint64_t* d_offsets,

@@ -10,6 +10,23 @@
 namespace rs {
 namespace {
 
+// Sec. 6.3 / 7.4: s_b and o_b of bucket b from the two Elias-Fano lists.
+__device__ __forceinline__ uint64_t ef_prefix(const View& v, uint64_t b) {
+  const uint64_t pa = ef_select(v, 0, b);
+  const uint64_t xa = ((pa - b) << v.low_a) | read_bits(v.lower, b * (v.low_a + v.low_b), v.low_a);
+  return xa + static_cast<uint64_t>(static_cast<int64_t>(b) * v.delta_a);
+}
+
+__device__ __forceinline__ uint64_t ef_offset(const View& v, uint64_t b, uint64_t s0) {
+  const uint64_t pb = ef_select(v, 1, b);
+  const uint64_t xb = ((pb - b) << v.low_b) | read_bits(v.lower, b * (v.low_a + v.low_b) + v.low_a, v.low_b);
+  const int64_t z = static_cast<int64_t>(xb) + static_cast<int64_t>(b) * v.delta_b;
+  const uint64_t bs = (__umul64hi(s0, v.beta) << 32) | ((s0 * v.beta) >> 32);
+  return static_cast<uint64_t>(z + static_cast<int64_t>(bs));
+}
+
+__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
+
 __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint64_t lo) {
   if (v.nb == 0) return 0;
   const uint64_t b = bucket_of(hi, v.nb);
@@ -21,14 +38,27 @@ __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint6
   const uint64_t xa1 = ((pa1 - b - 1) << v.low_a) | read_bits(v.lower, rec + rec_w, v.low_a);
   const uint64_t s0 = xa0 + static_cast<uint64_t>(static_cast<int64_t>(b) * v.delta_a);
   const uint64_t s1 = xa1 + static_cast<uint64_t>(static_cast<int64_t>(b + 1) * v.delta_a);
-  uint32_t m = static_cast<uint32_t>(s1 - s0);
+  const uint32_t m = static_cast<uint32_t>(s1 - s0);
   if (m <= 1) return s0;
-  const uint64_t pb = ef_select(v, 1, b);
-  const uint64_t xb = ((pb - b) << v.low_b) | read_bits(v.lower, rec + v.low_a, v.low_b);
-  const int64_t z = static_cast<int64_t>(xb) + static_cast<int64_t>(b) * v.delta_b;
-  const uint64_t bs = (__umul64hi(s0, v.beta) << 32) | ((s0 * v.beta) >> 32);
-  const uint64_t o = static_cast<uint64_t>(z + static_cast<int64_t>(bs));
+  return descend(v, s0, m, ef_offset(v, b, s0), lo);
+}
 
+// The same lookup with s_i, o_i of every bucket decoded beforehand (so[2i],
+// so[2i+1]; so[2N] = n): for batches with more queries than buckets.
+__device__ __forceinline__ uint64_t lookup_decoded(const View& v, const uint64_t* __restrict__ so, uint64_t hi,
+                                                   uint64_t lo) {
+  if (v.nb == 0) return 0;
+  const uint64_t b = bucket_of(hi, v.nb);
+  const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(so) + b);
+  const uint64_t s1 = __ldg(so + 2 * b + 2);
+  const uint32_t m = static_cast<uint32_t>(s1 - p.x);
+  if (m <= 1) return p.x;
+  return descend(v, p.x, m, p.y, lo);
+}
+
+// Sec. 4 / 6.2: descent of the splitting tree of a bucket of m keys whose
+// code starts at bit o.
+__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
   uint64_t fixed = o;
   uint64_t unary = o + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
   uint64_t c = 0;
@@ -59,21 +89,31 @@ __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint6
   }
 }
 
-__global__ void k_lookup_u64(View v, const uint64_t* __restrict__ keys, uint64_t q, uint64_t* __restrict__ out) {
-  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
-    uint64_t hi, lo;
-    signature_u64(__ldg(keys + i), hi, lo);
-    out[i] = lookup_one(v, hi, lo);
+// s_i and o_i of every bucket, one thread per element.
+__global__ void k_ef_decode(View v, uint64_t* __restrict__ so) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i <= v.nb; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t s = ef_prefix(v, i);
+    so[2 * i] = s;
+    so[2 * i + 1] = ef_offset(v, i, s);
   }
 }
 
-__global__ void k_lookup_bytes(View v, const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ offsets,
-                               uint64_t q, uint64_t* __restrict__ out) {
+__global__ void k_lookup_u64(View v, const uint64_t* __restrict__ so, const uint64_t* __restrict__ keys, uint64_t q,
+                             uint64_t* __restrict__ out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t hi, lo;
+    signature_u64(__ldg(keys + i), hi, lo);
+    out[i] = so ? lookup_decoded(v, so, hi, lo) : lookup_one(v, hi, lo);
+  }
+}
+
+__global__ void k_lookup_bytes(View v, const uint64_t* __restrict__ so, const uint8_t* __restrict__ bytes,
+                               const uint64_t* __restrict__ offsets, uint64_t q, uint64_t* __restrict__ out) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
     uint64_t hi, lo;
     signature_bytes(bytes + o0, o1 - o0, hi, lo);
-    out[i] = lookup_one(v, hi, lo);
+    out[i] = so ? lookup_decoded(v, so, hi, lo) : lookup_one(v, hi, lo);
   }
 }
 
@@ -149,7 +189,7 @@ View make_view(const Handle& h) {
   return v;
 }
 
-int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s) {
+int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s, bool allow_scratch) {
   if (q.n == 0) return RECSPLIT_OK;
   const View v = make_view(h);
   int dev = 0, sms = 0;
@@ -158,12 +198,25 @@ int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaSt
   const int block = 256;
   const uint64_t want = (q.n + block - 1) / block;
   const unsigned grid = static_cast<unsigned>(want < uint64_t(sms) * 64 ? want : uint64_t(sms) * 64);
+  // With at least as many queries as buckets, the prefix sums and offsets of
+  // all buckets are decoded once instead of selected per query (the stored
+  // structure does not change).  The scratch is allocated only then.
+  uint64_t* so = nullptr;
+  if (allow_scratch && v.nb && q.n >= v.nb + 1 && pool_alloc(reinterpret_cast<void**>(&so), 16 * (v.nb + 1), s) == RECSPLIT_OK) {
+    const uint64_t dg = (v.nb + 1 + block - 1) / block;
+    k_ef_decode<<<static_cast<unsigned>(dg < 65535 ? dg : 65535), block, 0, s>>>(v, so);
+    count_launch();
+  } else {
+    so = nullptr;
+  }
   if (q.u64)
-    k_lookup_u64<<<grid, block, 0, s>>>(v, q.u64, q.n, d_out);
+    k_lookup_u64<<<grid, block, 0, s>>>(v, so, q.u64, q.n, d_out);
   else
-    k_lookup_bytes<<<grid, block, 0, s>>>(v, q.bytes, q.offsets, q.n, d_out);
+    k_lookup_bytes<<<grid, block, 0, s>>>(v, so, q.bytes, q.offsets, q.n, d_out);
   count_launch();
-  RS_CUDA(cudaGetLastError());
+  const cudaError_t e = cudaGetLastError();
+  if (so) cudaFreeAsync(so, s);
+  if (e != cudaSuccess) return cuda_fail(e, "lookup launch");
   return RECSPLIT_OK;
 }
 

@@ -67,7 +67,7 @@ extern "C" int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* k
   KeyInput in;
   in.u64 = d_keys;
   in.n = q;
-  if ((rc = lookup_structure(*reinterpret_cast<const Handle*>(h), in, d_out, s))) return rc;
+  if ((rc = lookup_structure(*reinterpret_cast<const Handle*>(h), in, d_out, s, /*allow_scratch=*/false))) return rc;
   RS_CUDA(cudaMemcpyAsync(out, d_out, q * sizeof(uint64_t), cudaMemcpyDefault, s));
   RS_CUDA(cudaStreamSynchronize(s));
   return RECSPLIT_OK;
