@@ -31,27 +31,39 @@ __device__ __forceinline__ void signature_u64(uint64_t key, uint64_t& hi, uint64
 // Signature of a byte string: 8-byte little-endian words (zero padded)
 // absorbed by two mixer chains, the second on the word with its halves
 // swapped, then the length folded into both.  The string is read with
-// aligned 8-byte loads only; each loaded word holds at least one byte of the
-// string, so no load leaves the page that holds the string.
+// aligned 4-byte loads of the words that hold at least one of its bytes (no
+// load leaves the page that holds the string); each 8-byte word is two funnel
+// shifts of three consecutive loaded words.
 __device__ __forceinline__ void signature_bytes(const uint8_t* p, uint64_t len, uint64_t& hi, uint64_t& lo) {
   uint64_t a = kSigHi, c = kSigLo;
   if (len) {
     const uintptr_t addr = reinterpret_cast<uintptr_t>(p);
-    const uint64_t* w = reinterpret_cast<const uint64_t*>(addr & ~uintptr_t(7));
-    const uint32_t sh = static_cast<uint32_t>(addr & 7) * 8;
-    const uint64_t nwords_touched = ((addr + len - 1) >> 3) - (addr >> 3) + 1;
-    uint64_t cur = __ldg(w);
-    uint64_t k = 1;
-    for (uint64_t pos = 0; pos < len; pos += 8) {
-      uint64_t nxt = k < nwords_touched ? __ldg(w + k) : 0;
-      k++;
-      uint64_t word = sh ? ((cur >> sh) | (nxt << (64 - sh))) : cur;
-      const uint64_t rem = len - pos;
-      if (rem < 8) word &= (1ull << (8 * rem)) - 1;
-      const uint64_t swapped = (word >> 32) | (word << 32);
-      a = mix64(a ^ word);
-      c = mix64(c ^ swapped);
-      cur = nxt;
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(addr & ~uintptr_t(3));
+    const uint32_t sh = static_cast<uint32_t>(addr & 3) * 8;
+    const uint64_t nt = ((addr + len - 1) >> 2) - (addr >> 2) + 1;  // words touched
+    const uint64_t nfull = len >> 3;
+    uint32_t w0 = __ldg(w);
+    uint64_t j = 1;  // next word to load
+    // bytes 8i .. 8i + 7: words 2i (already loaded), 2i + 1 (always holds a
+    // byte of the string) and 2i + 2 (may hold none when sh == 0)
+    for (uint64_t i = 0; i < nfull; i++) {
+      const uint32_t w1 = __ldg(w + j);
+      const uint32_t w2 = j + 1 < nt ? __ldg(w + j + 1) : 0u;
+      j += 2;
+      const uint32_t l32 = __funnelshift_r(w0, w1, sh), h32 = __funnelshift_r(w1, w2, sh);
+      a = mix64(a ^ ((uint64_t(h32) << 32) | l32));
+      c = mix64(c ^ ((uint64_t(l32) << 32) | h32));
+      w0 = w2;
+    }
+    const uint32_t tail = static_cast<uint32_t>(len & 7);
+    if (tail) {
+      const uint32_t w1 = j < nt ? __ldg(w + j) : 0u;
+      const uint32_t w2 = j + 1 < nt ? __ldg(w + j + 1) : 0u;
+      uint32_t l32 = __funnelshift_r(w0, w1, sh), h32 = __funnelshift_r(w1, w2, sh);
+      if (tail < 4) l32 &= (1u << (8 * tail)) - 1;
+      h32 = tail <= 4 ? 0u : (h32 & ((1u << (8 * (tail - 4))) - 1));
+      a = mix64(a ^ ((uint64_t(h32) << 32) | l32));
+      c = mix64(c ^ ((uint64_t(l32) << 32) | h32));
     }
   }
   hi = mix64(a + len);
@@ -87,6 +99,19 @@ __device__ __forceinline__ uint32_t family_top32(uint64_t xpre, uint64_t kpre) {
 
 __device__ __forceinline__ uint32_t phi_pre(uint64_t xpre, uint64_t kpre, uint32_t m) {
   return __umulhi(family_top32(xpre, kpre), m);
+}
+
+// The same for a range fixed at compile time: for m = 2^k,
+// floor(h * 2^k / 2^32) is the top k bits of h (a shift, no multiply).
+__host__ __device__ constexpr int log2_exact(int m) { return m <= 1 ? 0 : 1 + log2_exact(m >> 1); }
+
+template <int M>
+__device__ __forceinline__ uint32_t phi_fixed(uint64_t xpre, uint64_t kpre) {
+  const uint32_t h = family_top32(xpre, kpre);
+  if constexpr (M >= 2 && (M & (M - 1)) == 0)
+    return h >> (32 - log2_exact(M));
+  else
+    return __umulhi(h, static_cast<uint32_t>(M));
 }
 
 // ---------------------------------------------------------------- bit arrays

@@ -56,33 +56,65 @@ __device__ __forceinline__ uint64_t lookup_decoded(const View& v, const uint64_t
   return descend(v, p.x, m, p.y, lo);
 }
 
+// Bit reads inside one bucket's code, with positions relative to the word
+// `t` that holds the code's first bit.  A bucket has at most 65535 keys and
+// every index is below 2^36 and below 1024 times its node's expected number
+// of trials, so a bucket's code is far shorter than 2^32 bits and positions
+// fit 32-bit registers.
+__device__ __forceinline__ uint32_t code_bits(const uint64_t* __restrict__ t, uint32_t pos, uint32_t width) {
+  const uint32_t w = pos >> 6, o = pos & 63;
+  uint64_t v = __ldg(t + w) >> o;
+  if (o + width > 64) v |= __ldg(t + w + 1) << (64 - o);
+  return static_cast<uint32_t>(v) & ((1u << width) - 1);  // width <= 31
+}
+
+__device__ __forceinline__ uint32_t code_next_one(const uint64_t* __restrict__ t, uint32_t pos) {
+  uint32_t w = pos >> 6;
+  uint64_t word = __ldg(t + w) & (~0ull << (pos & 63));
+  while (!word) word = __ldg(t + (++w));
+  return (w << 6) + static_cast<uint32_t>(__ffsll(static_cast<long long>(word)) - 1);
+}
+
+__device__ __forceinline__ uint32_t code_select(const uint64_t* __restrict__ t, uint32_t pos, uint32_t rank) {
+  uint32_t w = pos >> 6;
+  uint64_t word = __ldg(t + w) & (~0ull << (pos & 63));
+  for (;;) {
+    const uint32_t c = __popcll(word);
+    if (rank < c) break;
+    rank -= c;
+    word = __ldg(t + (++w));
+  }
+  return (w << 6) + select_in_word(word, rank);
+}
+
 // Sec. 4 / 6.2: descent of the splitting tree of a bucket of m keys whose
 // code starts at bit o.
 __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
-  uint64_t fixed = o;
-  uint64_t unary = o + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
-  uint64_t c = 0;
+  const uint64_t* __restrict__ t = v.tree + (o >> 6);
+  uint32_t fixed = static_cast<uint32_t>(o & 63);
+  uint32_t unary = fixed + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
+  uint32_t c = 0;
   const uint64_t xpre = pre_key(lo);
   for (uint32_t depth = 0;; depth++) {
     const uint64_t w1 = __ldg(v.table + kTableWords * m + 1);
     const uint32_t r = static_cast<uint32_t>(w1 >> 40) & 31;
     const uint32_t fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
     const uint32_t unit = static_cast<uint32_t>(w1);
-    const uint64_t low = read_bits(v.tree, fixed, r);
+    const uint32_t low = code_bits(t, fixed, r);
     fixed += r;
-    const uint64_t one = next_one(v.tree, unary);
-    const uint64_t seed = ((one - unary) << r) | low;
+    const uint32_t one = code_next_one(t, unary);
+    const uint64_t seed = (uint64_t(one - unary) << r) | low;
     unary = one + 1;
     const uint32_t val = phi_pre(xpre, family_key(seed, depth), m);
     if (fanout == 0) return s0 + c + val;
     const uint32_t magic = static_cast<uint32_t>(__ldg(v.table + kTableWords * m + 3));
-    const uint32_t part = min(magic && m < 65536 ? __umulhi(val, magic) : val / unit, fanout - 1);
+    const uint32_t part = min(magic ? __umulhi(val, magic) : val / unit, fanout - 1);
     if (part) {
       const uint64_t wu = __ldg(v.table + kTableWords * unit);
-      fixed += uint64_t(part) * static_cast<uint32_t>(wu);
-      const uint64_t skip = uint64_t(part) * (wu >> 32);
-      if (skip) unary = select_from(v.tree, unary, skip - 1) + 1;
-      c += uint64_t(part) * unit;
+      fixed += part * static_cast<uint32_t>(wu);
+      const uint32_t skip = part * static_cast<uint32_t>(wu >> 32);
+      if (skip) unary = code_select(t, unary, skip - 1) + 1;
+      c += part * unit;
     }
     m = part + 1 < fanout ? unit : m - unit * (fanout - 1);
     if (m <= 1) return s0 + c;

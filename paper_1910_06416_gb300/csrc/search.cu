@@ -69,15 +69,38 @@ __device__ __forceinline__ uint64_t trial_limit(const uint64_t* table, uint32_t 
 // Part t of a key is floor(phi / unit) (at most fanout - 1).  Counts of the
 // first fanout - 1 parts are packed in fields of B bits (2^B > m, so no field
 // overflows); success iff the packed sum equals the packed target.
+//
+// For fanouts of at most 4 the parts are not computed.  With h the top 32
+// bits of the hash, phi = floor(h * m / 2^32) < k * unit holds exactly when
+// h < T_k = ceil(k * unit * 2^32 / m) (T_k < 2^32 because k * unit < m), so
+// field k - 1 counts the keys with h < T_k, and the split is the one sought
+// iff field k - 1 equals k * unit for k = 1 .. fanout - 1.  This replaces two
+// multiply-highs and a variable shift per key by fanout - 1 compares.
 struct SplitParams {
   uint32_t m, unit, fanout, bits, magic;  // magic = ceil(2^32 / unit): exact for m < 2^16, unit >= 2
   uint64_t target, mask;
+  uint32_t thr[3];          // T_1 .. T_{fanout - 1} (threshold modes)
+  uint32_t inc1, inc2;      // 1 << B, 1 << 2B
+  uint32_t cum_target;      // sum over k of k * unit << ((k - 1) * B)
 };
 
-template <int MODE>  // 0: 32-bit fields + magic, 1: 64-bit fields + magic, 2: 64-bit + division
+// MODE 0: 32-bit fields + magic; 1: 64-bit fields + magic; 2: 64-bit +
+// division; 3, 4, 5: thresholds for fanout 2, 3, 4 (cumulative 32-bit fields).
+template <int MODE>
 __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, const SplitParams& p,
                                             uint64_t kp) {
-  if (MODE == 0) {
+  if (MODE >= 3) {
+    constexpr int F = MODE - 1;
+    uint32_t acc = 0;
+#pragma unroll 4
+    for (uint32_t j = 0; j < p.m; j++) {
+      const uint32_t h = family_top32(keys[j], kp);
+      acc += h < p.thr[0] ? 1u : 0u;
+      if (F > 2) acc += h < p.thr[1] ? p.inc1 : 0u;
+      if (F > 3) acc += h < p.thr[2] ? p.inc2 : 0u;
+    }
+    return acc == p.cum_target;
+  } else if (MODE == 0) {
     uint32_t acc = 0;
 #pragma unroll 4
     for (uint32_t j = 0; j < p.m; j++) {
@@ -152,12 +175,14 @@ __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ k
 __device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, const SplitParams& sp, int mode,
                                              uint32_t depth, uint32_t wig, uint32_t gwarps, uint32_t lane,
                                              uint64_t* best, uint64_t stall, uint64_t limit, int* err) {
-  if (mode == 0)
-    split_search_warp<0>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err);
-  else if (mode == 1)
-    split_search_warp<1>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err);
-  else
-    split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err);
+  switch (mode) {
+    case 0: split_search_warp<0>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 1: split_search_warp<1>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 3: split_search_warp<3>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 4: split_search_warp<4>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 5: split_search_warp<5>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    default: split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+  }
 }
 
 // Emits the children of a split node with at least two keys into the queues
@@ -222,7 +247,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
     sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
     // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
-    const int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+    int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+    if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= 4 && fields * sp.bits <= 32) {
+      mode = 1 + static_cast<int>(sp.fanout);
+      sp.cum_target = 0;
+      for (uint32_t k = 1; k <= fields; k++) {
+        sp.thr[k - 1] = static_cast<uint32_t>(((uint64_t(k * sp.unit) << 32) + nd.m - 1) / nd.m);
+        sp.cum_target += (k * sp.unit) << ((k - 1) * sp.bits);
+      }
+      sp.inc1 = 1u << sp.bits;
+      sp.inc2 = fields * sp.bits <= 32 && 2 * sp.bits < 32 ? 1u << (2 * sp.bits) : 0u;
+    }
     const uint64_t stall = stall_threshold(table, nd.m);
     const uint64_t limit = trial_limit(table, nd.m);
 
@@ -274,7 +309,7 @@ template <int L>
 __device__ __forceinline__ bool leaf_trial_full(const uint64_t (&x)[L], uint64_t kp) {
   uint32_t seen = 0;
 #pragma unroll
-  for (int j = 0; j < L; j++) seen |= 1u << phi_pre(x[j], kp, L);
+  for (int j = 0; j < L; j++) seen |= 1u << phi_fixed<L>(x[j], kp);
   return seen == (L == 32 ? ~0u : ((1u << L) - 1));
 }
 
@@ -299,7 +334,7 @@ __device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L],
     const uint64_t kp = family_key(base + off, depth);
     uint32_t seen = 0;
 #pragma unroll
-    for (int i = 0; i < H; i++) seen |= 1u << phi_pre(x[i], kp, L);
+    for (int i = 0; i < H; i++) seen |= 1u << phi_fixed<L>(x[i], kp);
     const bool ok = __popc(seen) == H;
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
     if (ok) surv[nsurv + __popc(b & ((1u << lane) - 1))] = make_uint2(off, seen);
@@ -314,7 +349,7 @@ __device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L],
       const uint64_t kp = family_key(base + e.x, depth);
       uint32_t seen = e.y;
 #pragma unroll
-      for (int i = H; i < L; i++) seen |= 1u << phi_pre(x[i], kp, L);
+      for (int i = H; i < L; i++) seen |= 1u << phi_fixed<L>(x[i], kp);
       ok = seen == full;
     }
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
