@@ -274,8 +274,14 @@ int recsplit_lookup_batch(const recsplit_t* const* hs, uint32_t count, const uin
   const bool dev = on_device(keys);
   if (on_device(ids) != dev || on_device(out) != dev)
     return fail(RECSPLIT_E_INVALID, "ids, keys and out must all be host or all device memory");
-  Staged v, k, d, o;
+  Staged v, k, d, o, so;
   int rc;
+  // large batches: every bucket's s_i, o_i decoded once (freed on return)
+  uint64_t* d_so = nullptr;
+  if ((rc = decode_views(views.data(), count, q, s, &d_so))) return rc;
+  so.dev = d_so;
+  so.owned = d_so != nullptr;
+  so.s = s;
   if ((rc = v.from(views.data(), count * sizeof(View), false, s))) return rc;
   if (!dev) {
     if ((rc = k.from(keys, q * sizeof(uint64_t), false, s)) || (rc = d.from(ids, q * sizeof(uint32_t), false, s)))

@@ -98,6 +98,7 @@ struct View {
   const uint64_t* anchors;
   const uint16_t* subs;
   const uint64_t* table;  // kTableWords words per size
+  const uint64_t* so;  // s_i, o_i of every bucket decoded beforehand, or null
   uint64_t nb;
   uint64_t beta;
   int64_t delta_a, delta_b;
@@ -170,6 +171,13 @@ int build_sets(const SetInput* sets, uint32_t count, const BuildOptions& opt, cu
 int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s, bool allow_scratch = true);
 int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
                 cudaStream_t s);
+// Batched lookups over several structures with at least as many queries as
+// the structures have buckets: s_i, o_i of every bucket of every structure
+// are decoded into one pooled array *so (the caller frees it, stream-ordered,
+// after the lookups) and views[i].so (host views) points at structure i's
+// part.  Otherwise, or if the memory is not available, *so stays null and the
+// views are unchanged (the lookups then select in the lists per query).
+int decode_views(View* views, uint32_t count, uint64_t q, cudaStream_t s, uint64_t** so);
 int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t* d_bytes, const uint64_t* d_offsets,
                       uint64_t q, uint64_t* d_out, cudaStream_t s);
 

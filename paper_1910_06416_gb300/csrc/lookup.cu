@@ -5,6 +5,8 @@
 // fixed parts are skipped with the table (a pointer move) and whose unary
 // parts are skipped by counting j * codes(unit) ones; at the leaf the
 // bijection's value is added to the keys left behind (c) and to s_b.
+#include <vector>
+
 #include "device.cuh"
 
 namespace rs {
@@ -149,12 +151,32 @@ __global__ void k_lookup_bytes(View v, const uint64_t* __restrict__ so, const ui
   }
 }
 
+// s_i and o_i of every bucket of every structure: element g of the global
+// index space belongs to the structure i with base[i] <= g < base[i + 1].
+__global__ void k_ef_decode_views(const View* __restrict__ views, const uint64_t* __restrict__ base, uint32_t count,
+                                  uint64_t total) {
+  for (uint64_t g = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; g < total; g += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t lo = 0, hi = count;  // last i with base[i] <= g
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (__ldg(base + mid) <= g) lo = mid; else hi = mid;
+    }
+    const View& v = views[lo];
+    const uint64_t e = g - __ldg(base + lo);
+    uint64_t* so = const_cast<uint64_t*>(v.so);
+    const uint64_t s = ef_prefix(v, e);
+    so[2 * e] = s;
+    so[2 * e + 1] = ef_offset(v, e, s);
+  }
+}
+
 __global__ void k_lookup_many(const View* __restrict__ views, const uint32_t* __restrict__ ids,
                               const uint64_t* __restrict__ keys, uint64_t q, uint64_t* __restrict__ out) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t hi, lo;
     signature_u64(__ldg(keys + i), hi, lo);
-    out[i] = lookup_one(views[__ldg(ids + i)], hi, lo);
+    const View& v = views[__ldg(ids + i)];
+    out[i] = v.so ? lookup_decoded(v, v.so, hi, lo) : lookup_one(v, hi, lo);
   }
 }
 
@@ -165,7 +187,8 @@ __global__ void k_lookup_many_bytes(const View* __restrict__ views, const uint32
     const uint64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
     uint64_t hi, lo;
     signature_bytes(bytes + o0, o1 - o0, hi, lo);
-    out[i] = lookup_one(views[__ldg(ids + i)], hi, lo);
+    const View& v = views[__ldg(ids + i)];
+    out[i] = v.so ? lookup_decoded(v, v.so, hi, lo) : lookup_one(v, hi, lo);
   }
 }
 
@@ -201,8 +224,49 @@ int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_ke
   return RECSPLIT_OK;
 }
 
+int decode_views(View* views, uint32_t count, uint64_t q, cudaStream_t s, uint64_t** so) {
+  *so = nullptr;
+  std::vector<uint64_t> base(count + 1);
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    base[i] = total;
+    total += views[i].nb ? views[i].nb + 1 : 0;
+  }
+  base[count] = total;
+  if (total == 0 || q < total + count) return RECSPLIT_OK;
+  void *d_so = nullptr, *d_views = nullptr, *d_base = nullptr;
+  if (pool_alloc(&d_so, 16 * total, s) != RECSPLIT_OK) return RECSPLIT_OK;  // fall back to per-query selects
+  for (uint32_t i = 0; i < count; i++) views[i].so = views[i].nb ? static_cast<uint64_t*>(d_so) + 2 * base[i] : nullptr;
+  int rc = pool_alloc(&d_views, sizeof(View) * count, s);
+  if (!rc) rc = pool_alloc(&d_base, sizeof(uint64_t) * (count + 1), s);
+  cudaError_t e = cudaSuccess;
+  if (!rc) e = cudaMemcpyAsync(d_views, views, sizeof(View) * count, cudaMemcpyHostToDevice, s);
+  if (!rc && e == cudaSuccess) e = cudaMemcpyAsync(d_base, base.data(), sizeof(uint64_t) * (count + 1),
+                                                   cudaMemcpyHostToDevice, s);
+  if (!rc && e == cudaSuccess) {
+    const uint64_t blocks = (total + 255) / 256;
+    k_ef_decode_views<<<static_cast<unsigned>(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(
+        static_cast<const View*>(d_views), static_cast<const uint64_t*>(d_base), count, total);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  // the pageable copies above complete before cudaMemcpyAsync returns, so the
+  // host arrays may go out of scope
+  if (d_views) cudaFreeAsync(d_views, s);
+  if (d_base) cudaFreeAsync(d_base, s);
+  if (rc || e != cudaSuccess) {
+    for (uint32_t i = 0; i < count; i++) views[i].so = nullptr;
+    cudaFreeAsync(d_so, s);
+    if (rc) return rc;
+    return cuda_fail(e, "decode of the Elias-Fano lists");
+  }
+  *so = static_cast<uint64_t*>(d_so);
+  return RECSPLIT_OK;
+}
+
 View make_view(const Handle& h) {
   View v;
+  v.so = nullptr;
   const uint64_t* H = h.header;
   v.tree = h.d_blob + h.layout.tree;
   v.lower = h.d_blob + h.layout.lower;

@@ -70,22 +70,26 @@ __device__ __forceinline__ uint64_t trial_limit(const uint64_t* table, uint32_t 
 // first fanout - 1 parts are packed in fields of B bits (2^B > m, so no field
 // overflows); success iff the packed sum equals the packed target.
 //
-// For fanouts of at most 4 the parts are not computed.  With h the top 32
+// For fanouts of at most 3 the parts are not computed.  With h the top 32
 // bits of the hash, phi = floor(h * m / 2^32) < k * unit holds exactly when
 // h < T_k = ceil(k * unit * 2^32 / m) (T_k < 2^32 because k * unit < m), so
 // field k - 1 counts the keys with h < T_k, and the split is the one sought
 // iff field k - 1 equals k * unit for k = 1 .. fanout - 1.  This replaces two
 // multiply-highs and a variable shift per key by fanout - 1 compares.
+// Largest fanout searched by thresholds: with three thresholds (fanout 4) the
+// compares cost about as much as the multiply-highs they replace.
+constexpr uint32_t kMaxThresholdFanout = 3;
+
 struct SplitParams {
   uint32_t m, unit, fanout, bits, magic;  // magic = ceil(2^32 / unit): exact for m < 2^16, unit >= 2
   uint64_t target, mask;
-  uint32_t thr[3];          // T_1 .. T_{fanout - 1} (threshold modes)
-  uint32_t inc1, inc2;      // 1 << B, 1 << 2B
+  uint32_t thr1, thr2;      // T_1, T_2 (threshold modes)
+  uint32_t inc1;            // 1 << B
   uint32_t cum_target;      // sum over k of k * unit << ((k - 1) * B)
 };
 
 // MODE 0: 32-bit fields + magic; 1: 64-bit fields + magic; 2: 64-bit +
-// division; 3, 4, 5: thresholds for fanout 2, 3, 4 (cumulative 32-bit fields).
+// division; 3, 4: thresholds for fanout 2, 3 (cumulative 32-bit fields).
 template <int MODE>
 __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, const SplitParams& p,
                                             uint64_t kp) {
@@ -95,9 +99,8 @@ __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, c
 #pragma unroll 4
     for (uint32_t j = 0; j < p.m; j++) {
       const uint32_t h = family_top32(keys[j], kp);
-      acc += h < p.thr[0] ? 1u : 0u;
-      if (F > 2) acc += h < p.thr[1] ? p.inc1 : 0u;
-      if (F > 3) acc += h < p.thr[2] ? p.inc2 : 0u;
+      acc += h < p.thr1 ? 1u : 0u;
+      if (F > 2) acc += h < p.thr2 ? p.inc1 : 0u;
     }
     return acc == p.cum_target;
   } else if (MODE == 0) {
@@ -180,7 +183,6 @@ __device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, 
     case 1: split_search_warp<1>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 3: split_search_warp<3>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 4: split_search_warp<4>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    case 5: split_search_warp<5>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     default: split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
   }
 }
@@ -248,15 +250,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
     // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
     int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
-    if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= 4 && fields * sp.bits <= 32) {
+    if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= kMaxThresholdFanout && fields * sp.bits <= 32) {
       mode = 1 + static_cast<int>(sp.fanout);
-      sp.cum_target = 0;
-      for (uint32_t k = 1; k <= fields; k++) {
-        sp.thr[k - 1] = static_cast<uint32_t>(((uint64_t(k * sp.unit) << 32) + nd.m - 1) / nd.m);
-        sp.cum_target += (k * sp.unit) << ((k - 1) * sp.bits);
-      }
+      // T_k = ceil(k * unit * 2^32 / m); field k - 1 must count k * unit keys
+      sp.thr1 = static_cast<uint32_t>(((uint64_t(sp.unit) << 32) + nd.m - 1) / nd.m);
+      sp.thr2 = static_cast<uint32_t>(((uint64_t(2 * sp.unit) << 32) + nd.m - 1) / nd.m);
+      sp.cum_target = sp.unit + (fields >= 2 ? (2 * sp.unit) << sp.bits : 0u);
       sp.inc1 = 1u << sp.bits;
-      sp.inc2 = fields * sp.bits <= 32 && 2 * sp.bits < 32 ? 1u << (2 * sp.bits) : 0u;
     }
     const uint64_t stall = stall_threshold(table, nd.m);
     const uint64_t limit = trial_limit(table, nd.m);

@@ -71,6 +71,14 @@ def test_small_batch_matches_oracle_and_single_builds(rs, orc):
         hout = np.zeros(ids.shape[0], dtype=np.uint64)
         rs.recsplit_lookup_batch(hs, ids, qk, hout)
         assert np.array_equal(hout, got)
+        # the batch above has more queries than the structures have buckets
+        # (lists decoded once); a small batch selects in the lists per query
+        buckets = sum(-(-n // b) + 1 for n, _, b, _ in plan if n)
+        few = 1000
+        assert few < buckets <= ids.shape[0] - len(plan)
+        out_few = torch.empty(few, dtype=torch.int64, device="cuda")
+        rs.recsplit_lookup_batch(hs, torch.from_numpy(ids[:few].view(np.int32)).cuda(), dev(qk[:few]), out_few)
+        assert np.array_equal(out_few.cpu().numpy().view(np.uint64), got[:few])
     finally:
         for h in hs:
             rs.recsplit_free(h)
