@@ -152,9 +152,10 @@ def nvtx_pop():
         pass
 
 
-def traffic_from_profiles(kernel_tag, source="search.cu"):
-    """DRAM bytes per launch recorded by an ncu capture summary, if the kernel
-    source has not changed since (else None)."""
+def traffic_from_profiles(kernel_tag, source="search.cu", key="dram_bytes_per_launch"):
+    """DRAM bytes recorded by an ncu capture summary (per launch, or with
+    key="dram_bytes_all_launches" summed over the captured launches), if the
+    kernel source has not changed since (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     src = os.path.join(ROOT, "paper_1910_06416_gb300", "csrc", source)
     if not os.path.exists(path):
@@ -168,7 +169,7 @@ def traffic_from_profiles(kernel_tag, source="search.cu"):
     if fields.get("source_sha256_16") != sha:
         return None
     try:
-        return float(fields["dram_bytes_per_launch"])
+        return float(fields[key])
     except (KeyError, ValueError):
         return None
 
@@ -383,7 +384,7 @@ def run_ours(a):
         "split_search": {"bound": "alu", "ms": split_ms,
                          "achieved": profs[-1]["split_evals"] * OPS_PER_SPLIT_EVAL / (split_ms / 1e3) / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s", "ops_per_eval": OPS_PER_SPLIT_EVAL,
-                         "peak_source": peak_src, "traffic": traffic_from_profiles(f"split_search_{tag}")},
+                         "peak_source": peak_src, "traffic": traffic_from_profiles(f"split_search_{tag}", key="dram_bytes_all_launches")},
         "lookup": {"bound": "hbm", "ms": look_ms_avg, "achieved": lookup_bytes / (look_ms_avg / 1e3) / 1e9,
                    "peak": hbm_peak,
                    "unit": "GB/s", "bytes_per_query": lookup_bytes / a.queries,

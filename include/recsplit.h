@@ -72,7 +72,10 @@ int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uin
 
 /* The same for n byte strings: key i is bytes[offsets[i] .. offsets[i+1]),
  * offsets has n + 1 non-decreasing entries (offsets[0] may be non-zero);
- * both arrays host or device (both in the same kind of memory). */
+ * both arrays host or device (both in the same kind of memory); bytes
+ * holds at least offsets[n] bytes.  Offsets that decrease fail with
+ * RECSPLIT_E_INVALID (checked on the device; no byte outside
+ * bytes[0 .. offsets[n]) is read). */
 int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
                          uint32_t bucket_size, void* stream, recsplit_t** out);
 
@@ -112,7 +115,8 @@ int recsplit_lookup_batch(const recsplit_t* const* hs, uint32_t count, const uin
  * (Sec. 1 allows any value).  keys and out: host or device. */
 int recsplit_lookup_u64(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
 
-/* Lookup of q byte strings, laid out as in recsplit_build_bytes. */
+/* Lookup of q byte strings, laid out as in recsplit_build_bytes.  A key
+ * with start > end or end > offsets[q] is read as the empty string. */
 int recsplit_lookup_bytes(const recsplit_t* h, const uint8_t* bytes, const uint64_t* offsets, uint64_t q,
                           uint64_t* out, void* stream);
 

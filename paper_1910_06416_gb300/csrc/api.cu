@@ -209,9 +209,10 @@ int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t
   if (n && on_device(bytes) != dev) return fail(RECSPLIT_E_INVALID, "bytes and offsets must both be host or device");
   Staged b, o;
   if (n && !dev) {
+    // bytes[0 .. offsets[n]) is copied; the device checks that the offsets
+    // do not decrease
+    if (offsets[n] < offsets[0]) return fail(RECSPLIT_E_INVALID, "byte-string offsets must not decrease");
     const uint64_t total = offsets[n];
-    for (uint64_t i = 0; i < n; i++)
-      if (offsets[i + 1] < offsets[i]) return fail(RECSPLIT_E_INVALID, "offsets must not decrease");
     if ((rc = b.from(bytes, total, false, s)) || (rc = o.from(offsets, (n + 1) * sizeof(uint64_t), false, s)))
       return rc;
   } else {
@@ -360,6 +361,7 @@ int recsplit_lookup_bytes(const recsplit_t* h, const uint8_t* bytes, const uint6
   if (q && (!bytes || !offsets || !out)) return fail(RECSPLIT_E_INVALID, "bytes, offsets or out is NULL");
   const bool dev = q && on_device(offsets);
   if (q && on_device(bytes) != dev) return fail(RECSPLIT_E_INVALID, "bytes and offsets must both be host or device");
+  if (q && !dev && offsets[q] < offsets[0]) return fail(RECSPLIT_E_INVALID, "byte-string offsets must not decrease");
   KeyInput in;
   in.bytes = bytes;
   in.offsets = offsets;

@@ -66,9 +66,14 @@ __device__ __forceinline__ uint32_t set_of_block(const DevSet* sets, uint32_t co
 
 // ---------------------------------------------------------------- A1/A2
 // Signature of every key, its global bucket, and the bucket histogram.
+// A byte-string key with start > end or end > offsets[n] (offsets must not
+// decrease) is read as the empty string and flags *bad_offsets: the build
+// then fails with RECSPLIT_E_INVALID, and no read leaves bytes[0 .. offsets[n]),
+// the span the caller provides.
 __global__ void __launch_bounds__(kBlock) k_signature(const DevSet* __restrict__ sets, uint32_t count,
                                                       uint32_t* __restrict__ bucket, uint64_t* __restrict__ lo,
-                                                      unsigned long long* __restrict__ counts) {
+                                                      unsigned long long* __restrict__ counts,
+                                                      int* __restrict__ bad_offsets) {
   const uint32_t si = set_of_block(sets, count, blockIdx.x, 0);
   const DevSet st = sets[si];
   const uint64_t t0 = (blockIdx.x - st.key_tile_base) * kTile;
@@ -81,7 +86,9 @@ __global__ void __launch_bounds__(kBlock) k_signature(const DevSet* __restrict__
       signature_u64(__ldg(st.u64 + j), h, l);
     } else {
       const uint64_t o0 = __ldg(st.offsets + j), o1 = __ldg(st.offsets + j + 1);
-      signature_bytes(st.bytes + o0, o1 - o0, h, l);
+      const bool ok = o0 <= o1 && o1 <= __ldg(st.offsets + st.n);
+      if (!ok) *bad_offsets = 1;
+      signature_bytes(st.bytes + (ok ? o0 : 0), ok ? o1 - o0 : 0, h, l);
     }
     const uint64_t b = st.bucket_base + bucket_of(h, st.nb);
     const uint64_t i = st.key_base + j;
@@ -521,10 +528,11 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   uint32_t *bucket, *bset;
   uint64_t *lo, *counts, *bstart, *codes, *cbase;
   unsigned long long *cls_max, *set_min, *set_max;
+  int* bad_offsets;
   if ((rc = sc.alloc(&d_sets, count)) || (rc = sc.alloc(&bucket, K)) || (rc = sc.alloc(&lo, K)) ||
       (rc = sc.alloc(&counts, NB + 1)) || (rc = sc.alloc(&bstart, NB + 1)) || (rc = sc.alloc(&codes, NB + 1)) ||
       (rc = sc.alloc(&cbase, NB + 1)) || (rc = sc.alloc(&bset, NB + 1)) || (rc = sc.alloc(&cls_max, kMaxClasses)) ||
-      (rc = sc.alloc(&set_min, count)) || (rc = sc.alloc(&set_max, count)))
+      (rc = sc.alloc(&set_min, count)) || (rc = sc.alloc(&set_max, count)) || (rc = sc.alloc(&bad_offsets, 1)))
     return rc;
   RS_CUDA(cudaMemcpyAsync(d_sets, hs.data(), count * sizeof(DevSet), cudaMemcpyHostToDevice, s));
 
@@ -533,9 +541,10 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   RS_CUDA(cudaMemsetAsync(cls_max, 0, kMaxClasses * sizeof(unsigned long long), s));
   RS_CUDA(cudaMemsetAsync(set_min, 0xFF, count * sizeof(unsigned long long), s));
   RS_CUDA(cudaMemsetAsync(set_max, 0, count * sizeof(unsigned long long), s));
+  RS_CUDA(cudaMemsetAsync(bad_offsets, 0, sizeof(int), s));
   if (key_tiles) {
-    k_signature<<<static_cast<unsigned>(key_tiles), kBlock, 0, s>>>(d_sets, count, bucket, lo,
-                                                                    reinterpret_cast<unsigned long long*>(counts));
+    k_signature<<<static_cast<unsigned>(key_tiles), kBlock, 0, s>>>(
+        d_sets, count, bucket, lo, reinterpret_cast<unsigned long long*>(counts), bad_offsets);
     count_launch();
   }
   if (bucket_tiles) {
@@ -550,7 +559,10 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
                           s));
   RS_CUDA(cudaMemcpyAsync(h_set_min.data(), set_min, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_set_max.data(), set_max, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  int h_bad = 0;
+  RS_CUDA(cudaMemcpyAsync(&h_bad, bad_offsets, sizeof(int), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaStreamSynchronize(s));  // sync 1: largest bucket per class
+  if (h_bad) return fail(RECSPLIT_E_INVALID, "byte-string offsets must not decrease");
 
   // tables per class, in one buffer
   std::vector<Tables> T(nclass);

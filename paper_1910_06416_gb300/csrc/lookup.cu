@@ -143,10 +143,12 @@ __global__ void k_lookup_u64(View v, const uint64_t* __restrict__ so, const uint
 
 __global__ void k_lookup_bytes(View v, const uint64_t* __restrict__ so, const uint8_t* __restrict__ bytes,
                                const uint64_t* __restrict__ offsets, uint64_t q, uint64_t* __restrict__ out) {
+  const uint64_t last = __ldg(offsets + q);  // the bytes span [0, offsets[q])
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
     uint64_t hi, lo;
-    signature_bytes(bytes + o0, o1 - o0, hi, lo);
+    const bool ok = o0 <= o1 && o1 <= last;  // else read as the empty string
+    signature_bytes(bytes + (ok ? o0 : 0), ok ? o1 - o0 : 0, hi, lo);
     out[i] = so ? lookup_decoded(v, so, hi, lo) : lookup_one(v, hi, lo);
   }
 }
@@ -183,10 +185,12 @@ __global__ void k_lookup_many(const View* __restrict__ views, const uint32_t* __
 __global__ void k_lookup_many_bytes(const View* __restrict__ views, const uint32_t* __restrict__ ids,
                                     const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ offsets,
                                     uint64_t q, uint64_t* __restrict__ out) {
+  const uint64_t last = __ldg(offsets + q);  // the bytes span [0, offsets[q])
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
     uint64_t hi, lo;
-    signature_bytes(bytes + o0, o1 - o0, hi, lo);
+    const bool ok = o0 <= o1 && o1 <= last;  // else read as the empty string
+    signature_bytes(bytes + (ok ? o0 : 0), ok ? o1 - o0 : 0, hi, lo);
     const View& v = views[__ldg(ids + i)];
     out[i] = v.so ? lookup_decoded(v, v.so, hi, lo) : lookup_one(v, hi, lo);
   }

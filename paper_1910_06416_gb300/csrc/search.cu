@@ -86,14 +86,19 @@ struct SplitParams {
   uint32_t thr1, thr2;      // T_1, T_2 (threshold modes)
   uint32_t inc1;            // 1 << B
   uint32_t cum_target;      // sum over k of k * unit << ((k - 1) * B)
+  uint32_t nbits, nmask, ntarget;  // narrow fields (mode 5): 2^nbits > unit
 };
 
 // MODE 0: 32-bit fields + magic; 1: 64-bit fields + magic; 2: 64-bit +
-// division; 3, 4: thresholds for fanout 2, 3 (cumulative 32-bit fields).
+// division; 3, 4: thresholds for fanout 2, 3 (cumulative 32-bit fields);
+// 5: 32-bit fields of nbits bits (2^nbits > unit but possibly <= m) + magic.
+// In mode 5 a field can overflow into the next one, so a match may be false,
+// but never missed: when every counted part has exactly unit keys no field
+// overflows.  A match is confirmed with the exact 64-bit count (mode 1).
 template <int MODE>
 __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, const SplitParams& p,
                                             uint64_t kp) {
-  if (MODE >= 3) {
+  if (MODE == 3 || MODE == 4) {
     constexpr int F = MODE - 1;
     uint32_t acc = 0;
 #pragma unroll 4
@@ -111,6 +116,14 @@ __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, c
       acc += shl32(1u, __umulhi(v, p.magic) * p.bits);
     }
     return (acc & static_cast<uint32_t>(p.mask)) == static_cast<uint32_t>(p.target);
+  } else if (MODE == 5) {
+    uint32_t acc = 0;
+#pragma unroll 4
+    for (uint32_t j = 0; j < p.m; j++) {
+      const uint32_t v = phi_pre(keys[j], kp, p.m);
+      acc += shl32(1u, __umulhi(v, p.magic) * p.nbits);
+    }
+    return (acc & p.nmask) == p.ntarget;
   } else {
     uint64_t acc = 0;
 #pragma unroll 4
@@ -166,7 +179,8 @@ __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ k
       }
     }
     const uint64_t kp = family_key(base + lane, depth);
-    const bool ok = split_trial<MODE>(keys, sp, kp);
+    bool ok = split_trial<MODE>(keys, sp, kp);
+    if (MODE == 5 && ok) ok = split_trial<1>(keys, sp, kp);
     const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
     if (hits) {
       if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(best), base + __ffs(hits) - 1);
@@ -183,6 +197,7 @@ __device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, 
     case 1: split_search_warp<1>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 3: split_search_warp<3>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 4: split_search_warp<4>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 5: split_search_warp<5>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     default: split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
   }
 }
@@ -250,6 +265,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
     // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
     int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+    if (mode == 1) {
+      sp.nbits = 32 - __clz(sp.unit);
+      if (fields * sp.nbits <= 32) {
+        mode = 5;
+        sp.nmask = fields * sp.nbits == 32 ? ~0u : (1u << (fields * sp.nbits)) - 1;
+        sp.ntarget = 0;
+        for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * sp.nbits);
+      }
+    }
     if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= kMaxThresholdFanout && fields * sp.bits <= 32) {
       mode = 1 + static_cast<int>(sp.fanout);
       // T_k = ceil(k * unit * 2^32 / m); field k - 1 must count k * unit keys
@@ -304,12 +328,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
 
 // ---------------------------------------------------------------- leaves
 // Leaf of exactly L keys (the common case): keys in registers, bijection
-// test as an OR of one-hot bits compared with 2^L - 1.
+// test as a sum of one-hot bits compared with 2^L - 1.  A sum of k powers of
+// two has k one bits only if no two of them are equal (every carry merges
+// two one bits), and 2^L - 1 has L one bits, so the sum of the L one-hot
+// values equals 2^L - 1 exactly when the values are distinct.  The sum, unlike
+// an OR, can be issued to the multiply-add pipe as well as the integer ALU.
 template <int L>
 __device__ __forceinline__ bool leaf_trial_full(const uint64_t (&x)[L], uint64_t kp) {
   uint32_t seen = 0;
 #pragma unroll
-  for (int j = 0; j < L; j++) seen |= 1u << phi_fixed<L>(x[j], kp);
+  for (int j = 0; j < L; j++) seen += 1u << phi_fixed<L>(x[j], kp);
   return seen == (L == 32 ? ~0u : ((1u << L) - 1));
 }
 
@@ -317,8 +345,8 @@ __device__ __forceinline__ bool leaf_trial_full(const uint64_t (&x)[L], uint64_t
 // for a leaf of exactly L keys.  Phase 1 maps the first H keys: an index whose
 // first H values are not distinct cannot be a bijection.  The survivors are
 // compacted, in index order, into the warp's shared buffer with their
-// partial one-hot masks; phase 2 finishes them on the last L - H keys, 32 at
-// a time.  The first survivor that completes 2^L - 1 is the smallest
+// partial one-hot sums (H one bits); phase 2 finishes them on the last L - H
+// keys, 32 at a time.  The first survivor that completes 2^L - 1 is the smallest
 // bijective index of the round.  Returns it, or ~0 if the round has none.
 __host__ __device__ constexpr int leaf_first_half(int l) { return (l + 1) / 2; }
 constexpr uint32_t kMaxSpl = 8;
@@ -334,7 +362,7 @@ __device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L],
     const uint64_t kp = family_key(base + off, depth);
     uint32_t seen = 0;
 #pragma unroll
-    for (int i = 0; i < H; i++) seen |= 1u << phi_fixed<L>(x[i], kp);
+    for (int i = 0; i < H; i++) seen += 1u << phi_fixed<L>(x[i], kp);
     const bool ok = __popc(seen) == H;
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
     if (ok) surv[nsurv + __popc(b & ((1u << lane) - 1))] = make_uint2(off, seen);
@@ -349,7 +377,7 @@ __device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L],
       const uint64_t kp = family_key(base + e.x, depth);
       uint32_t seen = e.y;
 #pragma unroll
-      for (int i = H; i < L; i++) seen |= 1u << phi_fixed<L>(x[i], kp);
+      for (int i = H; i < L; i++) seen += 1u << phi_fixed<L>(x[i], kp);
       ok = seen == full;
     }
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
@@ -369,7 +397,7 @@ __device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const
                                                 uint64_t kp) {
   uint32_t seen = 0;
 #pragma unroll
-  for (int j = 0; j < LMAX; j++) seen |= (1u << phi_pre(x[j], kp, m)) & keep[j];
+  for (int j = 0; j < LMAX; j++) seen += (1u << phi_pre(x[j], kp, m)) & keep[j];
   return seen == (1u << m) - 1;
 }
 

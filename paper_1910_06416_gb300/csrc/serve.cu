@@ -396,6 +396,7 @@ int recsplit_server_submit_build_bytes(recsplit_server_t* sp, const uint8_t* byt
   if (leaf_size < 1 || leaf_size > rs::kMaxLeaf || bucket_size < 1 || bucket_size > rs::kMaxBucket ||
       n >= (1ull << 32))
     return rs::fail(RECSPLIT_E_INVALID, "bad leaf size, bucket size or key count");
+  if (n && offsets[n] < offsets[0]) return rs::fail(RECSPLIT_E_INVALID, "byte-string offsets must not decrease");
   rs::Req r;
   r.kind = 0;
   r.bytes = bytes;
@@ -422,6 +423,7 @@ int recsplit_server_submit_lookup_u64(recsplit_server_t* sp, uint64_t structure_
 int recsplit_server_submit_lookup_bytes(recsplit_server_t* sp, uint64_t structure_id, const uint8_t* bytes,
                                         const uint64_t* offsets, uint64_t q, uint64_t* out, uint64_t* request_id) {
   if (!sp || (q && (!bytes || !offsets || !out))) return rs::fail(RECSPLIT_E_INVALID, "NULL argument");
+  if (q && offsets[q] < offsets[0]) return rs::fail(RECSPLIT_E_INVALID, "byte-string offsets must not decrease");
   rs::Req r;
   r.kind = 1;
   r.bytes = bytes;

@@ -148,6 +148,39 @@ def test_repeated_keys_are_reported(rs):
     assert ok.stats()["n"] == 1000
 
 
+def test_offsets_that_decrease_are_rejected(rs, orc):
+    """Builds reject offsets that decrease (host and device buffers, checked
+    on the device); lookups read such a key as the empty string and answer
+    every other key as usual."""
+    bk = inputs.byte_keys(3000, 28)
+    offs = bk.offsets.astype(np.uint64)
+    down = offs.copy()
+    down[101] = down[100] - 1  # key 100 ends before it starts
+    past = offs.copy()
+    past[50] = offs[-1] + 1000  # key 49 ends past the last offset
+    for bad in (down, past):
+        with pytest.raises(rs.RecSplitError) as e:
+            rs.Structure.build_bytes(bk.data, bad, 8, 100)
+        assert e.value.code == rs.E_INVALID
+        with pytest.raises(rs.RecSplitError) as e:
+            rs.Structure.build_bytes(torch.from_numpy(bk.data.copy()).cuda(), dev_u64(bad), 8, 100)
+        assert e.value.code == rs.E_INVALID
+    s = rs.Structure.build_bytes(bk.data, offs, 8, 100)  # still usable
+    assert_same_blob(s.serialize(), orc.build_bytes(bk.data, offs, 8, 100))
+    data = torch.from_numpy(bk.data.copy()).cuda()
+    good = torch.empty(3000, dtype=torch.int64, device="cuda")
+    s.lookup_bytes(data, dev_u64(offs), good)
+    got = torch.empty(3000, dtype=torch.int64, device="cuda")
+    s.lookup_bytes(data, dev_u64(down), got)
+    empty = torch.empty(1, dtype=torch.int64, device="cuda")
+    s.lookup_bytes(torch.zeros(1, dtype=torch.uint8, device="cuda"), dev_u64(np.zeros(2, dtype=np.uint64)), empty)
+    g, b = host_u64(good), host_u64(got)
+    keep = np.ones(3000, dtype=bool)
+    keep[[100, 101]] = False
+    assert np.array_equal(b[keep], g[keep])
+    assert b[100] == host_u64(empty)[0]
+
+
 def test_results_do_not_depend_on_key_order(rs):
     keys = inputs.u64_keys(60000, 27)
     a = gpu_build_u64(rs, keys, 8, 100).serialize()
