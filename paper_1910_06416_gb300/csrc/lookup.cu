@@ -58,50 +58,68 @@ __device__ __forceinline__ uint64_t lookup_decoded(const View& v, const uint64_t
   return descend(v, p.x, m, p.y, lo);
 }
 
-// Bit reads inside one bucket's code, with positions relative to the word
-// `t` that holds the code's first bit.  A bucket has at most 65535 keys and
-// every index is below 2^36 and below 1024 times its node's expected number
-// of trials, so a bucket's code is far shorter than 2^32 bits and positions
-// fit 32-bit registers.
-__device__ __forceinline__ uint32_t code_bits(const uint64_t* __restrict__ t, uint32_t pos, uint32_t width) {
-  const uint32_t w = pos >> 6, o = pos & 63;
-  uint64_t v = __ldg(t + w) >> o;
-  if (o + width > 64) v |= __ldg(t + w + 1) << (64 - o);
-  return static_cast<uint32_t>(v) & ((1u << width) - 1);  // width <= 31
+// Bit reads inside one bucket's code.  The tree bits are read as 32-bit
+// little-endian words (bit k of the vector is bit k mod 32 of 32-bit word
+// k / 32, the same bits as the 64-bit layout), with positions relative to the
+// 32-bit word `t` that holds the code's first bit.  A bucket has at most 65535
+// keys and every index is below 2^36 and below 1024 times its node's expected
+// number of trials, so a bucket's code is far shorter than 2^32 bits and
+// positions fit 32-bit registers.  32-bit words make every mask, shift, find
+// and count a single instruction.
+__device__ __forceinline__ uint32_t code_bits(const uint32_t* __restrict__ t, uint32_t pos, uint32_t width) {
+  const uint32_t w = pos >> 5, o = pos & 31;
+  const uint32_t lo = __ldg(t + w);
+  const uint32_t hi = o + width > 32 ? __ldg(t + w + 1) : 0u;
+  return __funnelshift_r(lo, hi, o) & ((1u << width) - 1);  // width <= 31
 }
 
-__device__ __forceinline__ uint32_t code_next_one(const uint64_t* __restrict__ t, uint32_t pos) {
-  uint32_t w = pos >> 6;
-  uint64_t word = __ldg(t + w) & (~0ull << (pos & 63));
+__device__ __forceinline__ uint32_t code_next_one(const uint32_t* __restrict__ t, uint32_t pos) {
+  uint32_t w = pos >> 5;
+  uint32_t word = __ldg(t + w) & (~0u << (pos & 31));
   while (!word) word = __ldg(t + (++w));
-  return (w << 6) + static_cast<uint32_t>(__ffsll(static_cast<long long>(word)) - 1);
+  return (w << 5) + static_cast<uint32_t>(__ffs(word) - 1);
 }
 
-__device__ __forceinline__ uint32_t code_select(const uint64_t* __restrict__ t, uint32_t pos, uint32_t rank) {
-  uint32_t w = pos >> 6;
-  uint64_t word = __ldg(t + w) & (~0ull << (pos & 63));
+// Position of the set bit of rank k (0-based) in a 32-bit word (k < popc).
+__device__ __forceinline__ uint32_t select_in_word32(uint32_t w, uint32_t k) {
+  uint32_t pos = 0, c = __popc(w & 0xFFFFu);
+  if (k >= c) { k -= c; pos = 16; w >>= 16; }
+  c = __popc(w & 0xFFu);
+  if (k >= c) { k -= c; pos += 8; w >>= 8; }
+  c = __popc(w & 0xFu);
+  if (k >= c) { k -= c; pos += 4; w >>= 4; }
+  c = __popc(w & 0x3u);
+  if (k >= c) { k -= c; pos += 2; w >>= 2; }
+  return pos + (k >= (w & 1u) ? 1u : 0u);
+}
+
+__device__ __forceinline__ uint32_t code_select(const uint32_t* __restrict__ t, uint32_t pos, uint32_t rank) {
+  uint32_t w = pos >> 5;
+  uint32_t word = __ldg(t + w) & (~0u << (pos & 31));
   for (;;) {
-    const uint32_t c = __popcll(word);
+    const uint32_t c = __popc(word);
     if (rank < c) break;
     rank -= c;
     word = __ldg(t + (++w));
   }
-  return (w << 6) + select_in_word(word, rank);
+  return (w << 5) + select_in_word32(word, rank);
 }
 
 // Sec. 4 / 6.2: descent of the splitting tree of a bucket of m keys whose
 // code starts at bit o.
 __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
-  const uint64_t* __restrict__ t = v.tree + (o >> 6);
-  uint32_t fixed = static_cast<uint32_t>(o & 63);
-  uint32_t unary = fixed + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
+  const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
+  uint32_t fixed = static_cast<uint32_t>(o & 31);
   uint32_t c = 0;
   const uint64_t xpre = pre_key(lo);
+  // words 0 and 1 of the node-size table: subtree fixed bits | codes << 32;
+  // unit | fanout << 32 | r << 40
+  ulonglong2 tw = __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * m));
+  uint32_t unary = fixed + static_cast<uint32_t>(tw.x);
   for (uint32_t depth = 0;; depth++) {
-    const uint64_t w1 = __ldg(v.table + kTableWords * m + 1);
-    const uint32_t r = static_cast<uint32_t>(w1 >> 40) & 31;
-    const uint32_t fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
-    const uint32_t unit = static_cast<uint32_t>(w1);
+    const uint32_t r = static_cast<uint32_t>(tw.y >> 40) & 31;
+    const uint32_t fanout = static_cast<uint32_t>(tw.y >> 32) & 0xFF;
+    const uint32_t unit = static_cast<uint32_t>(tw.y);
     const uint32_t low = code_bits(t, fixed, r);
     fixed += r;
     const uint32_t one = code_next_one(t, unary);
@@ -111,14 +129,17 @@ __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t
     if (fanout == 0) return s0 + c + val;
     const uint32_t magic = static_cast<uint32_t>(__ldg(v.table + kTableWords * m + 3));
     const uint32_t part = min(magic ? __umulhi(val, magic) : val / unit, fanout - 1);
+    const uint32_t next = part + 1 < fanout ? unit : m - unit * (fanout - 1);
+    const ulonglong2 tn = __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * next));
     if (part) {
-      const uint64_t wu = __ldg(v.table + kTableWords * unit);
-      fixed += part * static_cast<uint32_t>(wu);
-      const uint32_t skip = part * static_cast<uint32_t>(wu >> 32);
+      const ulonglong2 tu = part + 1 < fanout ? tn : __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * unit));
+      fixed += part * static_cast<uint32_t>(tu.x);
+      const uint32_t skip = part * static_cast<uint32_t>(tu.x >> 32);
       if (skip) unary = code_select(t, unary, skip - 1) + 1;
       c += part * unit;
     }
-    m = part + 1 < fanout ? unit : m - unit * (fanout - 1);
+    m = next;
+    tw = tn;
     if (m <= 1) return s0 + c;
   }
 }
