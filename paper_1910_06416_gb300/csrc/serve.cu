@@ -328,9 +328,15 @@ int recsplit_server_create(const recsplit_server_config_t* cfg, recsplit_server_
   s->cfg.hbm_budget_bytes = cfg && cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (64ull << 30);
   s->cfg.max_build_batch = cfg && cfg->max_build_batch ? cfg->max_build_batch : 64;
   s->cfg.max_lookup_batch = cfg && cfg->max_lookup_batch ? cfg->max_lookup_batch : (64ull << 20);
+  // Lookups run on a stream of the highest priority and builds on one of the
+  // lowest: the searches are persistent kernels that hold every SM for one
+  // tree level, so a lookup arriving during a build waits at most for the
+  // level in progress instead of for the rest of the build.
+  int least = 0, greatest = 0;
   if (cudaGetDevice(&s->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->sb, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->sl, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&s->sb, cudaStreamNonBlocking, least) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&s->sl, cudaStreamNonBlocking, greatest) != cudaSuccess) {
     int rc = rs::cuda_fail(cudaGetLastError(), "server streams");
     delete s;
     return rc;
