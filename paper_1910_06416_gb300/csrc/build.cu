@@ -20,6 +20,8 @@
 #include <cstring>
 #include <map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "device.cuh"
 
 namespace rs {
@@ -414,20 +416,31 @@ __global__ void k_code_leaf(const uint64_t* __restrict__ cbase, const uint32_t* 
   }
 }
 
+// Phase boundaries of a build: CUDA events on the build stream when
+// profiling is on, and always an NVTX range per phase (named
+// recsplit.signature, .group, .split, .leaves, .encode) around the launches
+// of that phase, so that a profiler can select one phase's kernels.
 struct PhaseTimer {
+  static constexpr const char* kNames[5] = {"recsplit.signature", "recsplit.group", "recsplit.split",
+                                            "recsplit.leaves", "recsplit.encode"};
   bool on;
   cudaStream_t s;
   cudaEvent_t ev[6] = {};
   int k = 0;
+  int ranges = 0;  // marks seen; a range is open while 1 <= ranges <= 5
   PhaseTimer(bool enabled, cudaStream_t stream) : on(enabled), s(stream) {
     if (on)
       for (auto& e : ev) cudaEventCreate(&e);
   }
   ~PhaseTimer() {
+    if (ranges >= 1 && ranges <= 5) nvtxRangePop();
     if (on)
       for (auto& e : ev) cudaEventDestroy(e);
   }
   void mark() {
+    if (ranges >= 1 && ranges <= 5) nvtxRangePop();
+    if (ranges < 5) nvtxRangePushA(kNames[ranges]);
+    ranges++;
     if (on && k < 6) cudaEventRecord(ev[k++], s);
   }
   double ms(int a, int b) const {

@@ -5,6 +5,8 @@
 // fixed parts are skipped with the table (a pointer move) and whose unary
 // parts are skipped by counting j * codes(unit) ones; at the leaf the
 // bijection's value is added to the keys left behind (c) and to s_b.
+#include <nvtx3/nvToolsExt.h>
+
 #include <vector>
 
 #include "device.cuh"
@@ -219,9 +221,16 @@ __global__ void k_lookup_many_bytes(const View* __restrict__ views, const uint32
 
 }  // namespace
 
+// NVTX range around the launches of one lookup call.
+struct LookupRange {
+  LookupRange() { nvtxRangePushA("recsplit.lookup"); }
+  ~LookupRange() { nvtxRangePop(); }
+};
+
 int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t* d_bytes, const uint64_t* d_offsets,
                       uint64_t q, uint64_t* d_out, cudaStream_t s) {
   if (q == 0) return RECSPLIT_OK;
+  LookupRange range;
   int dev = 0, sms = 0;
   RS_CUDA(cudaGetDevice(&dev));
   RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -237,6 +246,7 @@ int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t*
 int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
                 cudaStream_t s) {
   if (q == 0) return RECSPLIT_OK;
+  LookupRange range;
   int dev = 0, sms = 0;
   RS_CUDA(cudaGetDevice(&dev));
   RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -312,6 +322,7 @@ View make_view(const Handle& h) {
 
 int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s, bool allow_scratch) {
   if (q.n == 0) return RECSPLIT_OK;
+  LookupRange range;
   const View v = make_view(h);
   int dev = 0, sms = 0;
   RS_CUDA(cudaGetDevice(&dev));
