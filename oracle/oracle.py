@@ -55,6 +55,24 @@ def lib():
             L.orc_strategy.argtypes = [u32, u64, p, p, C.c_int]
             L.orc_log_success.restype = C.c_double
             L.orc_log_success.argtypes = [u32, u64]
+            L.orc_log_success_e.restype = C.c_double
+            L.orc_log_success_e.argtypes = [u32, u32, u64]
+            L.orc_golomb_rice_x_e.restype = C.c_double
+            L.orc_golomb_rice_x_e.argtypes = [u32, u32, u64]
+            L.orc_golomb_rice_e.restype = C.c_int
+            L.orc_golomb_rice_e.argtypes = [u32, u32, u64]
+            L.orc_node_range.restype = u64
+            L.orc_node_range.argtypes = [u32, u32, u64]
+            L.orc_leaf_seed_range.restype = i64
+            L.orc_leaf_seed_range.argtypes = [p, u64, u64, u32, u64]
+            L.orc_build_u64_e.restype = C.c_int
+            L.orc_build_u64_e.argtypes = [p, u64, u32, u32, u32, C.c_int, p, p]
+            L.orc_build_bytes_e.restype = C.c_int
+            L.orc_build_bytes_e.argtypes = [p, p, u64, u32, u32, u32, C.c_int, p, p]
+            L.orc_build_fingerprints_e.restype = C.c_int
+            L.orc_build_fingerprints_e.argtypes = [p, p, u64, u32, u32, u32, C.c_int, p, p]
+            L.orc_bucket_seeds_from_keys_e.restype = C.c_int
+            L.orc_bucket_seeds_from_keys_e.argtypes = [p, u64, u32, u32, p, p]
             L.orc_golomb_rice_x.restype = C.c_double
             L.orc_golomb_rice_x.argtypes = [u32, u64]
             L.orc_golomb_rice.restype = C.c_int
@@ -132,16 +150,29 @@ def strategy(leaf: int, m: int) -> list[int]:
     return [int(x) for x in parts[:f]]
 
 
-def log_success(leaf: int, m: int) -> float:
+def log_success(leaf: int, m: int, extra: int = 0) -> float:
+    """ln of one trial's success probability at a node of m keys (leaf
+    range m + extra for leaves)."""
+    if extra:
+        return float(lib().orc_log_success_e(leaf, extra, m))
     return float(lib().orc_log_success(leaf, m))
 
 
-def golomb_rice(leaf: int, m: int) -> int:
+def golomb_rice(leaf: int, m: int, extra: int = 0) -> int:
+    if extra:
+        return int(lib().orc_golomb_rice_e(leaf, extra, m))
     return int(lib().orc_golomb_rice(leaf, m))
 
 
-def golomb_rice_x(leaf: int, m: int) -> float:
+def golomb_rice_x(leaf: int, m: int, extra: int = 0) -> float:
+    if extra:
+        return float(lib().orc_golomb_rice_x_e(leaf, extra, m))
     return float(lib().orc_golomb_rice_x(leaf, m))
+
+
+def node_range(leaf: int, extra: int, m: int) -> int:
+    """Output range of the subtree of a node of m keys."""
+    return int(lib().orc_node_range(leaf, extra, m))
 
 
 def skip(leaf: int, m: int) -> tuple[int, int]:
@@ -151,8 +182,12 @@ def skip(leaf: int, m: int) -> tuple[int, int]:
     return int(fb[0]), int(nc[0])
 
 
-def leaf_seed(lo: np.ndarray, depth: int = 0, cap: int = 1 << 36) -> int:
+def leaf_seed(lo: np.ndarray, depth: int = 0, cap: int = 1 << 36, range_size: int | None = None) -> int:
+    """First index whose values on the leaf's keys are distinct in
+    [0, range_size) (default: the number of keys, a bijection)."""
     lo = np.ascontiguousarray(lo, dtype=np.uint64)
+    if range_size is not None:
+        return int(lib().orc_leaf_seed_range(_ptr(lo), lo.shape[0], range_size, depth, cap))
     return int(lib().orc_leaf_seed(_ptr(lo), lo.shape[0], depth, cap))
 
 
@@ -187,37 +222,48 @@ def _take_blob(blobp: C.c_void_p, words: np.ndarray) -> np.ndarray:
     return arr
 
 
-def build_fingerprints(hi, lo, leaf: int, bucket_size: int, threads: int = 1) -> np.ndarray:
+def build_fingerprints(hi, lo, leaf: int, bucket_size: int, threads: int = 1, extra: int = 0) -> np.ndarray:
     hi = np.ascontiguousarray(hi, dtype=np.uint64)
     lo = np.ascontiguousarray(lo, dtype=np.uint64)
     blobp, words = C.c_void_p(), np.zeros(1, dtype=np.uint64)
-    _check(lib().orc_build_fingerprints(_ptr(hi), _ptr(lo), hi.shape[0], leaf, bucket_size, threads,
-                                        C.byref(blobp), _ptr(words)))
+    _check(lib().orc_build_fingerprints_e(_ptr(hi), _ptr(lo), hi.shape[0], leaf, extra, bucket_size, threads,
+                                          C.byref(blobp), _ptr(words)))
     return _take_blob(blobp, words)
 
 
-def build_u64(keys: np.ndarray, leaf: int, bucket_size: int, threads: int = 1) -> np.ndarray:
-    """Serialized structure (uint64 words) for 64-bit keys."""
+def build_u64(keys: np.ndarray, leaf: int, bucket_size: int, threads: int = 1, extra: int = 0) -> np.ndarray:
+    """Serialized structure (uint64 words) for 64-bit keys; extra > 0 builds
+    the perfect, non-minimal variant (leaf ranges m + extra)."""
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     blobp, words = C.c_void_p(), np.zeros(1, dtype=np.uint64)
-    _check(lib().orc_build_u64(_ptr(keys), keys.shape[0], leaf, bucket_size, threads, C.byref(blobp),
-                               _ptr(words)))
+    if extra:
+        _check(lib().orc_build_u64_e(_ptr(keys), keys.shape[0], leaf, extra, bucket_size, threads,
+                                     C.byref(blobp), _ptr(words)))
+    else:
+        _check(lib().orc_build_u64(_ptr(keys), keys.shape[0], leaf, bucket_size, threads, C.byref(blobp),
+                                   _ptr(words)))
     return _take_blob(blobp, words)
 
 
 def build_bytes(data: np.ndarray, offsets: np.ndarray, leaf: int, bucket_size: int,
-                threads: int = 1) -> np.ndarray:
+                threads: int = 1, extra: int = 0) -> np.ndarray:
     data = np.ascontiguousarray(data, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
     blobp, words = C.c_void_p(), np.zeros(1, dtype=np.uint64)
-    _check(lib().orc_build_bytes(_ptr(data), _ptr(offsets), offsets.shape[0] - 1, leaf, bucket_size,
-                                 threads, C.byref(blobp), _ptr(words)))
+    if extra:
+        _check(lib().orc_build_bytes_e(_ptr(data), _ptr(offsets), offsets.shape[0] - 1, leaf, extra,
+                                       bucket_size, threads, C.byref(blobp), _ptr(words)))
+    else:
+        _check(lib().orc_build_bytes(_ptr(data), _ptr(offsets), offsets.shape[0] - 1, leaf, bucket_size,
+                                     threads, C.byref(blobp), _ptr(words)))
     return _take_blob(blobp, words)
 
 
 # ---------------------------------------------------------------- read
 def header(blob: np.ndarray) -> dict:
     h = {k: int(blob[i]) for i, k in enumerate(HEADER_FIELDS)}
+    h["leaf_extra"] = (h["leaf"] >> 8) & 0xFF  # word 2: leaf size | leaf range extra << 8
+    h["leaf"] &= 0xFF
     for k in ("delta_a", "delta_b"):
         if h[k] >= 1 << 63:
             h[k] -= 1 << 64
@@ -264,12 +310,12 @@ def decode_bucket(blob: np.ndarray, b: int) -> list[int]:
     return [int(x) for x in seeds[:int(cnt[0])]]
 
 
-def bucket_seeds(lo: np.ndarray, leaf: int) -> list[int]:
+def bucket_seeds(lo: np.ndarray, leaf: int, extra: int = 0) -> list[int]:
     """Preorder indices of the tree of one bucket whose keys have lower halves `lo`."""
     lo = np.ascontiguousarray(lo, dtype=np.uint64)
     seeds = np.zeros(max(1, lo.shape[0]), dtype=np.uint64)
     cnt = np.zeros(1, dtype=np.uint64)
-    _check(lib().orc_bucket_seeds_from_keys(_ptr(lo), lo.shape[0], leaf, _ptr(seeds), _ptr(cnt)))
+    _check(lib().orc_bucket_seeds_from_keys_e(_ptr(lo), lo.shape[0], leaf, extra, _ptr(seeds), _ptr(cnt)))
     return [int(x) for x in seeds[:int(cnt[0])]]
 
 

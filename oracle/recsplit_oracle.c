@@ -21,6 +21,13 @@
  *
  * The optional thread count of orc_build_* splits the buckets over POSIX
  * threads; buckets are independent (Sec. 4), so the bytes do not depend on it.
+ *
+ * The *_e functions also build the perfect, non-minimal variant the paper's
+ * conclusion leaves for future work (enlarged bijection codomains): with leaf
+ * range extra e > 0 a leaf of m >= 2 keys maps its keys injectively into
+ * [0, m + e) and everything downstream counts output ranges instead of keys
+ * (header word 2 holds the leaf size | e << 8).  e = 0 is the minimal
+ * structure, byte for byte.
  */
 #include <math.h>
 #include <pthread.h>
@@ -161,11 +168,18 @@ int orc_strategy(uint32_t leaf, uint64_t m, uint64_t* unit, uint64_t* parts, int
 /* Golomb-Rice parameters (Sec. 5.4 Eq. gr, Sec. 7.2) and skip tables. */
 /* ------------------------------------------------------------------ */
 /* ln of the success probability of one trial at a node of size m:
- * leaves m!/m^m (Sec. 5.2), splits Eq. probsplit (Sec. 5.1). */
-double orc_log_success(uint32_t leaf, uint64_t m) {
+ * leaves m!/m^m (Sec. 5.2), splits Eq. probsplit (Sec. 5.1).  With leaf
+ * range extra e > 0 (the perfect, non-minimal variant the conclusion of the
+ * paper sketches: the codomain of a leaf of m keys is enlarged to R = m + e)
+ * a leaf trial succeeds when the m values are distinct in [0, R):
+ * R! / ((R - m)! R^m).  e = 0 gives m!/m^m. */
+double orc_log_success_e(uint32_t leaf, uint32_t extra, uint64_t m) {
   double dm = (double)m;
+  if (m <= leaf) {
+    double dr = (double)(m + extra);
+    return lgamma(dr + 1.0) - lgamma(dr - dm + 1.0) - dm * log(dr);
+  }
   double lp = lgamma(dm + 1.0) - dm * log(dm);
-  if (m <= leaf) return lp;
   uint64_t parts[ORC_MAX_FANOUT], u;
   int f = orc_strategy(leaf, m, &u, parts, ORC_MAX_FANOUT);
   for (int j = 0; j < f; j++) {
@@ -175,13 +189,17 @@ double orc_log_success(uint32_t leaf, uint64_t m) {
   return lp;
 }
 
+double orc_log_success(uint32_t leaf, uint64_t m) { return orc_log_success_e(leaf, 0, m); }
+
 /* The real number whose ceiling (clamped at 0) is the parameter of Eq. gr:
  * lg(-lg(phi) / lg(1 - p)) = lg(ln(phi) / -ln(1 - p)). */
-double orc_golomb_rice_x(uint32_t leaf, uint64_t m) {
-  double p = exp(orc_log_success(leaf, m));
+double orc_golomb_rice_x_e(uint32_t leaf, uint32_t extra, uint64_t m) {
+  double p = exp(orc_log_success_e(leaf, extra, m));
   double golden = (1.0 + sqrt(5.0)) / 2.0;
   return log2(log(golden) / -log1p(-p));
 }
+
+double orc_golomb_rice_x(uint32_t leaf, uint64_t m) { return orc_golomb_rice_x_e(leaf, 0, m); }
 
 /* floor(lg x) for x >= 1, and 0 for x = 0 (lambda of Sec. 2). */
 static int orc_lambda(uint64_t x) {
@@ -196,10 +214,10 @@ static int orc_lambda(uint64_t x) {
 /* Golomb-Rice parameter of a node with m keys.  For m < 2^16 it is Eq. gr
  * evaluated in double; larger (split) nodes use the integer approximation of
  * Sec. 7.2, with ">>" read as a right shift as Sec. 7.1 uses it. */
-int orc_golomb_rice(uint32_t leaf, uint64_t m) {
+int orc_golomb_rice_e(uint32_t leaf, uint32_t extra, uint64_t m) {
   if (m <= 1) return 0;
   if (m < 65536) {
-    double x = orc_golomb_rice_x(leaf, m);
+    double x = orc_golomb_rice_x_e(leaf, extra, m);
     int r = (int)ceil(x);
     return r < 0 ? 0 : r;
   }
@@ -212,51 +230,93 @@ int orc_golomb_rice(uint32_t leaf, uint64_t m) {
   return (int)(acc >> 1);
 }
 
+int orc_golomb_rice(uint32_t leaf, uint64_t m) { return orc_golomb_rice_e(leaf, 0, m); }
+
 typedef struct {
   uint32_t leaf;
+  uint32_t extra;  /* leaf range extra e (0: minimal)                */
   uint64_t mmax;
   int* r;          /* Golomb-Rice parameter per node size            */
   uint64_t* fbits; /* fixed bits of the subtree of a node of size m  */
   uint64_t* codes; /* number of codes (indices) in that subtree      */
+  uint64_t* rng;   /* output range of that subtree: the sum of its leaves' ranges
+                      (m + e for a leaf of m >= 2 keys, m for 0 or 1 key) */
 } orc_tables;
 
 static void orc_tables_free(orc_tables* t) {
   free(t->r);
   free(t->fbits);
   free(t->codes);
+  free(t->rng);
 }
 
 /* Sec. 6.2 skip information: for every size m the fixed bits and the number
  * of codes of a whole subtree.  Sizes 0 and 1 carry no code (Fig. 1). */
-static int orc_tables_init(orc_tables* t, uint32_t leaf, uint64_t mmax) {
+static int orc_tables_init(orc_tables* t, uint32_t leaf, uint32_t extra, uint64_t mmax) {
   t->leaf = leaf;
+  t->extra = extra;
   t->mmax = mmax;
   t->r = calloc(mmax + 1, sizeof(int));
   t->fbits = calloc(mmax + 1, sizeof(uint64_t));
   t->codes = calloc(mmax + 1, sizeof(uint64_t));
-  if (!t->r || !t->fbits || !t->codes) {
+  t->rng = calloc(mmax + 1, sizeof(uint64_t));
+  if (!t->r || !t->fbits || !t->codes || !t->rng) {
     orc_tables_free(t);
     return ORC_E_NOMEM;
   }
+  t->rng[0] = 0;
+  if (mmax >= 1) t->rng[1] = 1;
   for (uint64_t m = 2; m <= mmax; m++) {
-    t->r[m] = orc_golomb_rice(leaf, m);
+    t->r[m] = orc_golomb_rice_e(leaf, extra, m);
     t->fbits[m] = (uint64_t)t->r[m];
     t->codes[m] = 1;
+    t->rng[m] = m + extra;
     if (m > leaf) {
       uint64_t parts[ORC_MAX_FANOUT], u;
       int f = orc_strategy(leaf, m, &u, parts, ORC_MAX_FANOUT);
+      t->rng[m] = 0;
       for (int j = 0; j < f; j++) {
         t->fbits[m] += t->fbits[parts[j]];
         t->codes[m] += t->codes[parts[j]];
+        t->rng[m] += t->rng[parts[j]];
       }
+    }
+    /* a bucket's size is read back from its range, so the range must grow
+     * strictly with the size; this is checked for every size */
+    if (t->rng[m] <= t->rng[m - 1]) {
+      orc_tables_free(t);
+      return ORC_E_INVALID;
     }
   }
   return ORC_OK;
 }
 
+/* The node size whose subtree has output range R, or UINT64_MAX. */
+static uint64_t orc_size_of_range(const orc_tables* t, uint64_t R) {
+  uint64_t a = 0, b = t->mmax;
+  while (a < b) {
+    uint64_t mid = (a + b + 1) / 2;
+    if (t->rng[mid] <= R)
+      a = mid;
+    else
+      b = mid - 1;
+  }
+  return t->rng[a] == R ? a : UINT64_MAX;
+}
+
+/* Output range of the subtree of a node of m keys with leaf range extra e
+ * (m itself for e = 0), or 0 if the tables cannot be made. */
+uint64_t orc_node_range(uint32_t leaf, uint32_t extra, uint64_t m) {
+  orc_tables t;
+  if (orc_tables_init(&t, leaf, extra, m < 2 ? 2 : m)) return 0;
+  uint64_t r = t.rng[m];
+  orc_tables_free(&t);
+  return r;
+}
+
 int orc_skip(uint32_t leaf, uint64_t m, uint64_t* fixed_bits, uint64_t* codes) {
   orc_tables t;
-  if (orc_tables_init(&t, leaf, m < 2 ? 2 : m)) return ORC_E_NOMEM;
+  if (orc_tables_init(&t, leaf, 0, m < 2 ? 2 : m)) return ORC_E_NOMEM;
   *fixed_bits = m < 2 ? 0 : t.fbits[m];
   *codes = m < 2 ? 0 : t.codes[m];
   orc_tables_free(&t);
@@ -266,13 +326,15 @@ int orc_skip(uint32_t leaf, uint64_t m, uint64_t* fixed_bits, uint64_t* codes) {
 /* ------------------------------------------------------------------ */
 /* Brute-force searches (Sec. 4).                                      */
 /* ------------------------------------------------------------------ */
-/* First i such that phi^m_i maps the m keys of a leaf onto [0, m). */
-int64_t orc_leaf_seed(const uint64_t* lo, uint64_t m, uint32_t depth, uint64_t cap) {
+/* First i such that phi^R_i maps the m keys of a leaf to m distinct values
+ * of [0, R): for R = m a bijection onto [0, m) (Sec. 4), for R > m an
+ * injection (the perfect, non-minimal variant).  R <= 64. */
+int64_t orc_leaf_seed_range(const uint64_t* lo, uint64_t m, uint64_t R, uint32_t depth, uint64_t cap) {
   for (uint64_t i = 0; i < cap; i++) {
     uint64_t seen = 0;
     int ok = 1;
     for (uint64_t j = 0; j < m; j++) {
-      uint64_t bit = 1ULL << orc_phi(lo[j], depth, i, m);
+      uint64_t bit = 1ULL << orc_phi(lo[j], depth, i, R);
       if (seen & bit) {
         ok = 0; /* two keys on one value: not a bijection */
         break;
@@ -282,6 +344,10 @@ int64_t orc_leaf_seed(const uint64_t* lo, uint64_t m, uint32_t depth, uint64_t c
     if (ok) return (int64_t)i;
   }
   return -1;
+}
+
+int64_t orc_leaf_seed(const uint64_t* lo, uint64_t m, uint32_t depth, uint64_t cap) {
+  return orc_leaf_seed_range(lo, m, m, depth, cap);
 }
 
 /* First i such that, mapping the m keys to [0, m) with phi^m_i, exactly k_t
@@ -320,7 +386,7 @@ static int orc_solve(const orc_tables* t, uint64_t* keys, uint64_t m, uint32_t d
   if (m <= 1) return ORC_OK;
   if (depth > 63) return ORC_E_INVALID;
   if (m <= t->leaf) {
-    int64_t s = orc_leaf_seed(keys, m, depth, ORC_MAX_TRIALS);
+    int64_t s = orc_leaf_seed_range(keys, m, m + t->extra, depth, ORC_MAX_TRIALS);
     if (s < 0) return ORC_E_SEARCH_LIMIT;
     seeds[*pos] = (uint64_t)s;
     sizes[*pos] = m;
@@ -361,15 +427,15 @@ static int orc_cmp_u64(const void* a, const void* b) {
 /* Preorder indices of one bucket given the lower signature halves of its
  * keys.  Keys sharing their lower half can never be separated (Sec. 7.3
  * works on the lower half only), so they are reported as duplicates. */
-int orc_bucket_seeds_from_keys(const uint64_t* lo, uint64_t m, uint32_t leaf, uint64_t* seeds,
-                               uint64_t* count) {
-  if (leaf < 1 || leaf > 24) return ORC_E_INVALID;
+int orc_bucket_seeds_from_keys_e(const uint64_t* lo, uint64_t m, uint32_t leaf, uint32_t extra, uint64_t* seeds,
+                                 uint64_t* count) {
+  if (leaf < 1 || leaf > 24 || leaf + extra > 32) return ORC_E_INVALID;
   uint64_t* keys = malloc((m + 1) * sizeof(uint64_t));
   uint64_t* tmp = malloc((m + 1) * sizeof(uint64_t));
   uint64_t* sizes = malloc((m + 1) * sizeof(uint64_t));
   orc_tables t;
   int rc = ORC_E_NOMEM;
-  if (!keys || !tmp || !sizes || orc_tables_init(&t, leaf, m < 2 ? 2 : m)) goto out_nomem;
+  if (!keys || !tmp || !sizes || orc_tables_init(&t, leaf, extra, m < 2 ? 2 : m)) goto out_nomem;
   memcpy(keys, lo, m * sizeof(uint64_t));
   qsort(keys, m, sizeof(uint64_t), orc_cmp_u64);
   rc = ORC_OK;
@@ -383,6 +449,10 @@ out_nomem:
   free(tmp);
   free(sizes);
   return rc;
+}
+
+int orc_bucket_seeds_from_keys(const uint64_t* lo, uint64_t m, uint32_t leaf, uint64_t* seeds, uint64_t* count) {
+  return orc_bucket_seeds_from_keys_e(lo, m, leaf, 0, seeds, count);
 }
 
 /* ------------------------------------------------------------------ */
@@ -463,10 +533,16 @@ static void orc_layout_of(const uint64_t* h, orc_layout* L) {
 }
 
 /* Build from signatures.  On success *blob receives a malloc'ed array of
- * *words 64-bit words holding the serialized structure. */
-int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, uint32_t leaf,
-                           uint32_t bucket_size, int threads, uint64_t** blob, uint64_t* words) {
-  if (leaf < 1 || leaf > 24 || bucket_size < 1 || bucket_size > 65535) return ORC_E_INVALID;
+ * *words 64-bit words holding the serialized structure.  extra = 0 builds
+ * the minimal perfect hash function of the paper.  extra = e > 0 builds the
+ * perfect, non-minimal variant: every leaf of m >= 2 keys maps its keys
+ * injectively into m + e values, a bucket's output range is the sum of its
+ * leaves' ranges, and the first Elias-Fano list holds the prefix sums of the
+ * bucket ranges instead of the bucket sizes (a bucket's size is the one
+ * whose range is the difference).  leaf + extra <= 32. */
+int orc_build_fingerprints_e(const uint64_t* hi, const uint64_t* lo, uint64_t n, uint32_t leaf, uint32_t extra,
+                             uint32_t bucket_size, int threads, uint64_t** blob, uint64_t* words) {
+  if (leaf < 1 || leaf > 24 || bucket_size < 1 || bucket_size > 65535 || leaf + extra > 32) return ORC_E_INVALID;
   if (threads < 1) threads = 1;
   uint64_t nb = (n + bucket_size - 1) / bucket_size;
   int rc = ORC_E_NOMEM;
@@ -475,7 +551,7 @@ int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, u
   uint64_t* bstart = calloc(nb + 2, sizeof(uint64_t));
   uint64_t* sorted = malloc((n + 1) * sizeof(uint64_t));
   uint64_t* fill = calloc(nb + 1, sizeof(uint64_t));
-  uint64_t *cbase = NULL, *seeds = NULL, *sizes = NULL, *bits = NULL, *out = NULL;
+  uint64_t *cbase = NULL, *seeds = NULL, *sizes = NULL, *bits = NULL, *out = NULL, *rstart = NULL;
   orc_tables t;
   int have_tables = 0;
   if (!bstart || !sorted || !fill) goto done;
@@ -490,8 +566,14 @@ int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, u
     uint64_t b = orc_bucket(hi[i], nb);
     sorted[bstart[b] + fill[b]++] = lo[i];
   }
-  if (orc_tables_init(&t, leaf, mmax < 2 ? 2 : mmax)) goto done;
+  if ((rc = orc_tables_init(&t, leaf, extra, mmax < 2 ? 2 : mmax))) goto done;
   have_tables = 1;
+  rc = ORC_E_NOMEM;
+  /* prefix sums of the bucket output ranges (the bucket sizes when e = 0) */
+  rstart = calloc(nb + 2, sizeof(uint64_t));
+  if (!rstart) goto done;
+  for (uint64_t b = 0; b < nb; b++) rstart[b + 1] = rstart[b] + t.rng[bstart[b + 1] - bstart[b]];
+  uint64_t nrange = rstart[nb];
 
   /* Code slots: bucket b owns codes(m_b) consecutive slots. */
   cbase = calloc(nb + 1, sizeof(uint64_t));
@@ -568,8 +650,9 @@ int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, u
     }
   }
 
-  /* Sec. 6.3 / Sec. 7.4: double Elias-Fano of s_i and o_i - beta s_i. */
-  uint64_t beta = n ? (uint64_t)(((u128)T << 32) / n) : 0;
+  /* Sec. 6.3 / Sec. 7.4: double Elias-Fano of s_i and o_i - beta s_i (with
+   * the range prefix sums in place of s_i in the non-minimal variant). */
+  uint64_t beta = nrange ? (uint64_t)(((u128)T << 32) / nrange) : 0;
   uint64_t* xa = malloc((nb + 1) * sizeof(uint64_t));
   int64_t* z = malloc((nb + 1) * sizeof(int64_t));
   uint64_t* xb = malloc((nb + 1) * sizeof(uint64_t));
@@ -583,16 +666,16 @@ int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, u
   }
   int64_t da = 0, db = 0;
   for (uint64_t i = 0; i < nb; i++) {
-    int64_t d = (int64_t)(bstart[i + 1] - bstart[i]);
+    int64_t d = (int64_t)(rstart[i + 1] - rstart[i]);
     if (i == 0 || d < da) da = d;
   }
-  for (uint64_t i = 0; i <= nb; i++) z[i] = (int64_t)off[i] - (int64_t)(((u128)bstart[i] * beta) >> 32);
+  for (uint64_t i = 0; i <= nb; i++) z[i] = (int64_t)off[i] - (int64_t)(((u128)rstart[i] * beta) >> 32);
   for (uint64_t i = 0; i < nb; i++) {
     int64_t d = z[i + 1] - z[i];
     if (i == 0 || d < db) db = d;
   }
   for (uint64_t i = 0; i <= nb; i++) {
-    xa[i] = bstart[i] - (uint64_t)((int64_t)i * da);
+    xa[i] = rstart[i] - (uint64_t)((int64_t)i * da);
     xb[i] = (uint64_t)(z[i] - (int64_t)i * db);
   }
   int la = orc_ef_width(xa[nb], nb + 1), lb = orc_ef_width(xb[nb], nb + 1);
@@ -601,7 +684,7 @@ int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, u
   uint64_t h[ORC_HEADER_WORDS] = {0};
   h[0] = ORC_MAGIC;
   h[1] = n;
-  h[2] = leaf;
+  h[2] = leaf | ((uint64_t)extra << 8);
   h[3] = bucket_size;
   h[4] = nb;
   h[5] = T;
@@ -667,6 +750,28 @@ done:
   free(sizes);
   free(bits);
   free(out);
+  free(rstart);
+  return rc;
+}
+
+int orc_build_fingerprints(const uint64_t* hi, const uint64_t* lo, uint64_t n, uint32_t leaf,
+                           uint32_t bucket_size, int threads, uint64_t** blob, uint64_t* words) {
+  return orc_build_fingerprints_e(hi, lo, n, leaf, 0, bucket_size, threads, blob, words);
+}
+
+int orc_build_u64_e(const uint64_t* keys, uint64_t n, uint32_t leaf, uint32_t extra, uint32_t bucket_size,
+                    int threads, uint64_t** blob, uint64_t* words) {
+  uint64_t* hi = malloc((n + 1) * sizeof(uint64_t));
+  uint64_t* lo = malloc((n + 1) * sizeof(uint64_t));
+  if (!hi || !lo) {
+    free(hi);
+    free(lo);
+    return ORC_E_NOMEM;
+  }
+  orc_fingerprint_u64(keys, n, hi, lo);
+  int rc = orc_build_fingerprints_e(hi, lo, n, leaf, extra, bucket_size, threads, blob, words);
+  free(hi);
+  free(lo);
   return rc;
 }
 
@@ -697,6 +802,22 @@ int orc_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, u
   }
   orc_fingerprint_bytes(bytes, offsets, n, hi, lo);
   int rc = orc_build_fingerprints(hi, lo, n, leaf, bucket_size, threads, blob, words);
+  free(hi);
+  free(lo);
+  return rc;
+}
+
+int orc_build_bytes_e(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf, uint32_t extra,
+                      uint32_t bucket_size, int threads, uint64_t** blob, uint64_t* words) {
+  uint64_t* hi = malloc((n + 1) * sizeof(uint64_t));
+  uint64_t* lo = malloc((n + 1) * sizeof(uint64_t));
+  if (!hi || !lo) {
+    free(hi);
+    free(lo);
+    return ORC_E_NOMEM;
+  }
+  orc_fingerprint_bytes(bytes, offsets, n, hi, lo);
+  int rc = orc_build_fingerprints_e(hi, lo, n, leaf, extra, bucket_size, threads, blob, words);
   free(hi);
   free(lo);
   return rc;
@@ -776,9 +897,14 @@ int orc_decode_bucket(const uint64_t* blob, uint64_t b, uint64_t* seeds, uint64_
   uint64_t s0, s1, o0, o1;
   orc_bucket_info(blob, b, &s0, &o0);
   orc_bucket_info(blob, b + 1, &s1, &o1);
-  uint64_t m = s1 - s0;
   orc_tables t;
-  if (orc_tables_init(&t, (uint32_t)blob[2], blob[6] < 2 ? 2 : blob[6])) return ORC_E_NOMEM;
+  int rct = orc_tables_init(&t, (uint32_t)(blob[2] & 0xFF), (uint32_t)((blob[2] >> 8) & 0xFF), blob[6] < 2 ? 2 : blob[6]);
+  if (rct) return rct;
+  uint64_t m = orc_size_of_range(&t, s1 - s0);
+  if (m == UINT64_MAX) {
+    orc_tables_free(&t);
+    return ORC_E_INVALID;
+  }
   /* preorder list of node sizes, expanded with an explicit stack */
   uint64_t* stack = malloc((64 * ORC_MAX_FANOUT + 1) * sizeof(uint64_t));
   uint64_t sp = 0, k = 0;
@@ -815,23 +941,26 @@ typedef struct {
 static int orc_reader_init(orc_reader* rd, const uint64_t* blob) {
   if (blob[0] != ORC_MAGIC) return ORC_E_INVALID;
   rd->n = blob[1];
-  rd->leaf = blob[2];
+  rd->leaf = blob[2] & 0xFF;
   rd->nb = blob[4];
   orc_layout_of(blob, &rd->L);
-  return orc_tables_init(&rd->t, (uint32_t)rd->leaf, blob[6] < 2 ? 2 : blob[6]);
+  return orc_tables_init(&rd->t, (uint32_t)rd->leaf, (uint32_t)((blob[2] >> 8) & 0xFF), blob[6] < 2 ? 2 : blob[6]);
 }
 
 /* Sec. 4: descend from the root with the split indices; every move to
  * child j leaves the j earlier siblings (and their keys) to the left, whose
  * fixed bits are skipped with the table and whose unary codes are skipped by
- * counting ones (Sec. 6.2); at the leaf add the bijection's value. */
+ * counting ones (Sec. 6.2); at the leaf add the bijection's value.  In the
+ * non-minimal variant the siblings left behind count with their output
+ * ranges and the leaf's value lies in [0, m + e). */
 static uint64_t orc_lookup_one(const orc_reader* rd, const uint64_t* blob, uint64_t hi, uint64_t lo) {
   if (rd->nb == 0) return 0;
   uint64_t b = orc_bucket(hi, rd->nb);
   uint64_t s0, s1, o0, o1;
   orc_bucket_info(blob, b, &s0, &o0);
   orc_bucket_info(blob, b + 1, &s1, &o1);
-  uint64_t m = s1 - s0;
+  uint64_t m = orc_size_of_range(&rd->t, s1 - s0);
+  if (m == UINT64_MAX) return s0;  /* not a structure this reader wrote */
   const uint64_t* tree = blob + rd->L.tree;
   uint64_t fpos = o0, upos = o0 + (m < 2 ? 0 : rd->t.fbits[m]), c = 0;
   uint32_t depth = 0;
@@ -842,8 +971,8 @@ static uint64_t orc_lookup_one(const orc_reader* rd, const uint64_t* blob, uint6
     fpos += (uint64_t)r;
     uint64_t q = orc_next_unary(tree, &upos);
     uint64_t seed = (q << r) | low;
+    if (m <= rd->leaf) return s0 + c + orc_phi(lo, depth, seed, m + rd->t.extra);
     uint64_t v = orc_phi(lo, depth, seed, m);
-    if (m <= rd->leaf) return s0 + c + v;
     uint64_t parts[ORC_MAX_FANOUT], u;
     int f = orc_strategy((uint32_t)rd->leaf, m, &u, parts, ORC_MAX_FANOUT);
     uint64_t lim = 0;
@@ -856,7 +985,7 @@ static uint64_t orc_lookup_one(const orc_reader* rd, const uint64_t* blob, uint6
     for (int j = 0; j < p; j++) {
       fpos += rd->t.fbits[parts[j]];
       for (uint64_t skip = rd->t.codes[parts[j]]; skip; skip--) orc_next_unary(tree, &upos);
-      c += parts[j];
+      c += rd->t.rng[parts[j]];
     }
     m = parts[p];
     depth++;
