@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--leaf", type=int, default=8)
     ap.add_argument("--bucket", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="strings", choices=["strings", "u64", "batch", "sweep"],
+    ap.add_argument("--workload", default="strings", choices=["strings", "u64", "batch", "sweep", "perfect"],
                     help="strings: byte-string keys (default workload); u64: 64-bit keys (seed 0 for leaf 5, "
                          "seed 2 otherwise); batch: 4096 sets of log-uniform sizes with mixed leaf/bucket sizes")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -612,6 +612,48 @@ def run_sweep(a):
     return 0
 
 
+def run_perfect(a):
+    """Perfect, non-minimal variant: 10^7 64-bit keys (seed 6), l = 8,
+    b = 100, leaf range extra e in {0, 1, 2, 4, 8}: build keys/s, bits/key,
+    output range per key and 10^8 member lookups/s for each e."""
+    import torch
+
+    from paper_1910_06416_gb300 import build as lib_build, inputs
+    import paper_1910_06416_gb300.recsplit as rs
+
+    lib_build.build()
+    rs.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n, q = 10_000_000, 100_000_000
+    keys = torch.from_numpy(inputs.u64_keys(n, 6).view(np.int64)).to(dev)
+    queries = keys[torch.from_numpy(inputs.query_indices(n, q, 6)).to(dev)]
+    out = torch.empty(q, dtype=torch.int64, device=dev)
+    rs.recsplit_autotune(8, 100, n, stream.cuda_stream)
+    rs.recsplit_set_profiling(True)
+    rows = []
+    for extra in (0, 1, 2, 4, 8):
+        bt, lt = [], []
+        for rep in range(4):
+            h = rs.recsplit_build_perfect_u64(keys, 8, 100, extra, stream.cuda_stream)
+            bt.append(rs.recsplit_last_profile()["ms_total"])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs.recsplit_lookup_u64(h, queries, out, stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lt.append(e0.elapsed_time(e1))
+            st = rs.recsplit_stats(h)
+            rs.recsplit_free(h)
+        b_ms, l_ms = statistics.median(bt[1:]), statistics.median(lt[1:])
+        rows.append({"leaf_extra": extra, "build_ms": b_ms, "keys_per_s": n / (b_ms / 1e3),
+                     "bits_per_key": st["bits_per_key"], "tree_bits_per_key": st["tree_bits_per_key"],
+                     "range_per_key": st["range_size"] / n, "lookups_per_s": q / (l_ms / 1e3)})
+    print(json.dumps({"metric": "perfect (non-minimal) variant over the leaf range extra", "workload": "perfect",
+                      "n": n, "leaf_size": 8, "bucket_size": 100, "queries": q, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -620,6 +662,8 @@ def main():
         return run_u64(a)
     if a.workload == "batch":
         return run_batch(a)
+    if a.workload == "perfect":
+        return run_perfect(a)
     if a.workload == "sweep":
         return run_sweep(a)
     return run_ours(a)

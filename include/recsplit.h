@@ -61,6 +61,10 @@ typedef struct recsplit_stats {
   uint64_t num_codes;     /* number of stored split/bijection indices         */
   double tree_bits_per_key;
   double bits_per_key;    /* total_bits / n                                   */
+  uint32_t leaf_extra;    /* leaf range extra e (0: minimal perfect hash)     */
+  uint32_t reserved;
+  uint64_t range_size;    /* lookups of the n keys are distinct values in
+                             [0, range_size); range_size = n when e = 0     */
 } recsplit_stats_t;
 
 /* Build from n 64-bit keys (Sec. 4).  keys: n uint64 values, host or device.
@@ -78,6 +82,24 @@ int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uin
  * bytes[0 .. offsets[n]) is read). */
 int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
                          uint32_t bucket_size, void* stream, recsplit_t** out);
+
+/* Perfect, non-minimal variant (the conclusion of the paper notes that
+ * enlarging the codomain of the bijections gives compact perfect hash
+ * functions, and leaves the construction to future work; this is one reading
+ * of it).  Splits are as in recsplit_build_u64; every leaf of m >= 2 keys maps
+ * its keys injectively into [0, m + leaf_extra) (the first index whose values
+ * are distinct there), which needs far fewer trials than a bijection.  The
+ * lookups of the n keys are distinct values in [0, range_size), with
+ * range_size (recsplit_stats) the sum over all leaves of their ranges.
+ * leaf_extra = 0 gives exactly recsplit_build_u64's structure;
+ * leaf_size + leaf_extra <= 32, else RECSPLIT_E_INVALID.  Lookups use
+ * recsplit_lookup_u64 / _bytes (the header records leaf_extra). */
+int recsplit_build_perfect_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size,
+                               uint32_t leaf_extra, void* stream, recsplit_t** out);
+
+/* The same for byte strings, laid out as in recsplit_build_bytes. */
+int recsplit_build_perfect_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
+                                 uint32_t bucket_size, uint32_t leaf_extra, void* stream, recsplit_t** out);
 
 /* recsplit_build_u64 under the short name of the construction call. */
 int recsplit_build(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
@@ -306,6 +328,11 @@ int recsplit_inject_alloc_failure(int64_t after);
  * rule of Sec. 7.2 from 2^16 keys on): out[m] for m in [0, m_hi], host
  * memory, m_hi + 1 entries.  Host-only; for inspection and tests. */
 int recsplit_golomb_rice_params(uint32_t leaf_size, uint64_t m_hi, uint8_t* out);
+
+/* The same for the perfect, non-minimal variant: leaves of m keys use the
+ * success probability of an injection into [0, m + leaf_extra),
+ * (m + e)! / (e! (m + e)^m).  leaf_extra = 0 gives recsplit_golomb_rice_params. */
+int recsplit_golomb_rice_params_extra(uint32_t leaf_size, uint32_t leaf_extra, uint64_t m_hi, uint8_t* out);
 
 #ifdef __cplusplus
 }

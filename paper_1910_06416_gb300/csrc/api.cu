@@ -175,10 +175,11 @@ using namespace rs;
 
 extern "C" {
 
-int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
-                       recsplit_t** out) {
+static int build_u64_impl(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size,
+                          uint32_t leaf_extra, void* stream, recsplit_t** out) {
   int rc = check_build_args(n, leaf_size, bucket_size, out);
   if (rc) return rc;
+  if (leaf_extra > 32 - leaf_size) return fail(RECSPLIT_E_INVALID, "leaf_size + leaf_extra must be at most 32");
   if (n && !keys) return fail(RECSPLIT_E_INVALID, "keys is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Staged k;
@@ -188,10 +189,21 @@ int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uin
   in.keys.n = n;
   in.leaf = leaf_size;
   in.bucket_size = bucket_size;
+  in.leaf_extra = leaf_extra;
   Handle* h = nullptr;
   if ((rc = build_sets(&in, 1, BuildOptions{}, s, &h))) return rc;
   *out = reinterpret_cast<recsplit_t*>(h);
   return RECSPLIT_OK;
+}
+
+int recsplit_build_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
+                       recsplit_t** out) {
+  return build_u64_impl(keys, n, leaf_size, bucket_size, 0, stream, out);
+}
+
+int recsplit_build_perfect_u64(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size,
+                               uint32_t leaf_extra, void* stream, recsplit_t** out) {
+  return build_u64_impl(keys, n, leaf_size, bucket_size, leaf_extra, stream, out);
 }
 
 int recsplit_build(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size, void* stream,
@@ -199,10 +211,11 @@ int recsplit_build(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_
   return recsplit_build_u64(keys, n, leaf_size, bucket_size, stream, out);
 }
 
-int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
-                         uint32_t bucket_size, void* stream, recsplit_t** out) {
+static int build_bytes_impl(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
+                            uint32_t bucket_size, uint32_t leaf_extra, void* stream, recsplit_t** out) {
   int rc = check_build_args(n, leaf_size, bucket_size, out);
   if (rc) return rc;
+  if (leaf_extra > 32 - leaf_size) return fail(RECSPLIT_E_INVALID, "leaf_size + leaf_extra must be at most 32");
   if (n && (!offsets || !bytes)) return fail(RECSPLIT_E_INVALID, "bytes or offsets is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool dev = n && on_device(offsets);
@@ -225,10 +238,21 @@ int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t
   in.keys.n = n;
   in.leaf = leaf_size;
   in.bucket_size = bucket_size;
+  in.leaf_extra = leaf_extra;
   Handle* h = nullptr;
   if ((rc = build_sets(&in, 1, BuildOptions{}, s, &h))) return rc;
   *out = reinterpret_cast<recsplit_t*>(h);
   return RECSPLIT_OK;
+}
+
+int recsplit_build_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
+                         uint32_t bucket_size, void* stream, recsplit_t** out) {
+  return build_bytes_impl(bytes, offsets, n, leaf_size, bucket_size, 0, stream, out);
+}
+
+int recsplit_build_perfect_bytes(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, uint32_t leaf_size,
+                                 uint32_t bucket_size, uint32_t leaf_extra, void* stream, recsplit_t** out) {
+  return build_bytes_impl(bytes, offsets, n, leaf_size, bucket_size, leaf_extra, stream, out);
 }
 
 int recsplit_build_batch(const recsplit_keyset_t* sets, uint32_t count, void* stream, recsplit_t** outs) {
@@ -388,7 +412,8 @@ int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t**
   uint64_t H[kHeaderWords];
   std::memcpy(H, buf, sizeof(H));
   if (H[H_MAGIC] != kMagic) return fail(RECSPLIT_E_INVALID, "bad magic");
-  if (H[H_LEAF] < 1 || H[H_LEAF] > kMaxLeaf || H[H_BUCKET] < 1 || H[H_BUCKET] > kMaxBucket ||
+  if (header_leaf(H) < 1 || header_leaf(H) > kMaxLeaf || (H[H_LEAF] >> 16) != 0 ||
+      header_extra(H) > 32 - header_leaf(H) || H[H_BUCKET] < 1 || H[H_BUCKET] > kMaxBucket ||
       H[H_N] >= (1ull << 32) || H[H_NB] != (H[H_N] + H[H_BUCKET] - 1) / H[H_BUCKET] || H[H_LOW_A] > 63 ||
       H[H_LOW_B] > 63 || H[H_MMAX] > H[H_N])
     return fail(RECSPLIT_E_INVALID, "inconsistent header");
@@ -397,7 +422,7 @@ int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t**
     return fail(RECSPLIT_E_INVALID, "size does not match the header");
   Tables T;
   std::string err;
-  int rc = build_tables(static_cast<uint32_t>(H[H_LEAF]), H[H_MMAX], &T, &err);
+  int rc = build_tables(header_leaf(H), header_extra(H), H[H_MMAX], &T, &err);
   if (rc) return fail(rc, err);
   Handle* h = new Handle();
   std::memcpy(h->header, H, sizeof(H));
@@ -422,6 +447,23 @@ int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t**
     return rc;
   }
   h->ncodes = H[H_CODES];
+  // output range: the last element of the first Elias-Fano list, whose
+  // upper bits end the upper-bits array (Sec. 7.4), plus the rescaling
+  {
+    const uint64_t* w = static_cast<const uint64_t*>(buf);
+    const uint64_t nb = H[H_NB], la = H[H_LOW_A];
+    uint64_t low = 0;
+    if (la) {
+      const uint64_t pos = nb * (la + H[H_LOW_B]);
+      const uint64_t* lower = w + L.lower;
+      low = lower[pos >> 6] >> (pos & 63);
+      if ((pos & 63) + la > 64) low |= lower[(pos >> 6) + 1] << (64 - (pos & 63));
+      low &= la == 64 ? ~0ull : ((1ull << la) - 1);
+    }
+    const uint64_t xa_last = H[H_UP_A] >= nb + 1 ? ((H[H_UP_A] - 1 - nb) << la) | low : 0;
+    h->range_size = nb ? xa_last + static_cast<uint64_t>(static_cast<int64_t>(nb) * static_cast<int64_t>(H[H_DELTA_A]))
+                       : 0;
+  }
   *out = reinterpret_cast<recsplit_t*>(h);
   return RECSPLIT_OK;
 }
@@ -431,7 +473,9 @@ int recsplit_stats(const recsplit_t* hp, recsplit_stats_t* st) {
   const Handle* h = as_handle(hp);
   const uint64_t* H = h->header;
   st->n = H[H_N];
-  st->leaf_size = static_cast<uint32_t>(H[H_LEAF]);
+  st->leaf_size = header_leaf(H);
+  st->leaf_extra = header_extra(H);
+  st->range_size = h->range_size;
   st->bucket_size = static_cast<uint32_t>(H[H_BUCKET]);
   st->num_buckets = H[H_NB];
   st->tree_bits = H[H_TBITS];

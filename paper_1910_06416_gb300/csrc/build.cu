@@ -137,12 +137,14 @@ __global__ void __launch_bounds__(kBlock) k_bucket_sets(const DevSet* __restrict
 // Per set: tree bits and number of codes (differences of the global scans at
 // the set's first and one-past-last bucket).
 __global__ void k_set_scalars(const DevSet* __restrict__ sets, uint32_t count, const uint64_t* __restrict__ off,
-                              const uint64_t* __restrict__ cbase, uint64_t* __restrict__ tree_bits,
-                              uint64_t* __restrict__ ncodes) {
+                              const uint64_t* __restrict__ cbase, const uint64_t* __restrict__ rstart,
+                              uint64_t* __restrict__ tree_bits, uint64_t* __restrict__ ncodes,
+                              uint64_t* __restrict__ nrange) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const uint64_t b0 = sets[i].bucket_base, b1 = b0 + sets[i].nb;
     tree_bits[i] = off[b1] - off[b0];
     ncodes[i] = cbase[b1] - cbase[b0];
+    nrange[i] = rstart[b1] - rstart[b0];
   }
 }
 
@@ -157,6 +159,15 @@ __global__ void k_bucket_codes(const uint64_t* __restrict__ counts, const uint32
                                uint64_t* __restrict__ codes) {
   for (uint64_t b = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; b < nbt; b += uint64_t(gridDim.x) * blockDim.x)
     codes[b] = ct.t[sets[bset[b]].cls][kTableWords * counts[b]] >> 32;
+}
+
+// Output range of every bucket (table word 3, upper half): the sum of its
+// leaves' ranges, which is the bucket size when the leaf range extra is 0.
+__global__ void k_bucket_ranges(const uint64_t* __restrict__ counts, const uint32_t* __restrict__ bset,
+                                const DevSet* __restrict__ sets, uint64_t nbt, ClassTables ct,
+                                uint64_t* __restrict__ ranges) {
+  for (uint64_t b = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; b < nbt; b += uint64_t(gridDim.x) * blockDim.x)
+    ranges[b] = ct.t[sets[bset[b]].cls][kTableWords * counts[b] + 3] >> 32;
 }
 
 // Sec. 9: grouping by bucket; the order inside a bucket does not matter
@@ -228,23 +239,26 @@ __device__ __forceinline__ uint64_t beta_of(uint64_t tree_bits, uint64_t n) {
 }
 
 // Per set: the smallest difference of consecutive values o_i - beta s_i.
+// rstart: prefix sums of the bucket output ranges (of the bucket sizes when
+// the leaf range extra is 0), global over all sets.
 __global__ void __launch_bounds__(kBlock) k_ef_prepare(const DevSet* __restrict__ sets, uint32_t count,
-                                                       const uint64_t* __restrict__ bstart,
+                                                       const uint64_t* __restrict__ rstart,
                                                        const uint64_t* __restrict__ off,
                                                        long long* __restrict__ set_db) {
   const uint32_t si = set_of_block(sets, count, blockIdx.x, 1);
   const DevSet st = sets[si];
   const uint64_t bb = st.bucket_base;
   const uint64_t T = off[bb + st.nb] - off[bb];
-  const uint64_t beta = beta_of(T, st.n);
+  const uint64_t r0 = rstart[bb];
+  const uint64_t beta = beta_of(T, rstart[bb + st.nb] - r0);
   const uint64_t t0 = (blockIdx.x - st.bucket_tile_base) * kTile;
   long long mn = LLONG_MAX;
   for (int k = 0; k < kTileItems; k++) {
     const uint64_t j = t0 + uint64_t(k) * kBlock + threadIdx.x;
     if (j < st.nb) {
-      const long long z0 = (long long)(off[bb + j] - off[bb]) - (long long)mulhi32_shift(bstart[bb + j] - st.key_base, beta);
+      const long long z0 = (long long)(off[bb + j] - off[bb]) - (long long)mulhi32_shift(rstart[bb + j] - r0, beta);
       const long long z1 =
-          (long long)(off[bb + j + 1] - off[bb]) - (long long)mulhi32_shift(bstart[bb + j + 1] - st.key_base, beta);
+          (long long)(off[bb + j + 1] - off[bb]) - (long long)mulhi32_shift(rstart[bb + j + 1] - r0, beta);
       mn = min(mn, z1 - z0);
     }
   }
@@ -334,9 +348,9 @@ __global__ void k_write_codes(const uint64_t* __restrict__ counts, const uint64_
 }
 
 // ---------------------------------------------------------------- A7
-__device__ __forceinline__ void ef_values(const DevSet& st, const DevOut& p, const uint64_t* bstart,
+__device__ __forceinline__ void ef_values(const DevSet& st, const DevOut& p, const uint64_t* rstart,
                                           const uint64_t* off, uint64_t i, uint64_t& xa, uint64_t& xb) {
-  const uint64_t s = bstart[st.bucket_base + i] - st.key_base;
+  const uint64_t s = rstart[st.bucket_base + i] - rstart[st.bucket_base];
   const int64_t z = (int64_t)(off[st.bucket_base + i] - off[st.bucket_base]) - (int64_t)mulhi32_shift(s, p.beta);
   xa = s - static_cast<uint64_t>((int64_t)i * p.delta_a);
   xb = static_cast<uint64_t>(z - (int64_t)i * p.delta_b);
@@ -346,7 +360,7 @@ __device__ __forceinline__ void ef_values(const DevSet& st, const DevOut& p, con
 // u64 / u16 inventories of both lists.
 __global__ void __launch_bounds__(kBlock) k_ef_write(const DevSet* __restrict__ sets, uint32_t count,
                                                      const DevOut* __restrict__ outs,
-                                                     const uint64_t* __restrict__ bstart,
+                                                     const uint64_t* __restrict__ rstart,
                                                      const uint64_t* __restrict__ off) {
   const uint32_t si = set_of_block(sets, count, blockIdx.x, 2);
   const DevSet st = sets[si];
@@ -356,7 +370,7 @@ __global__ void __launch_bounds__(kBlock) k_ef_write(const DevSet* __restrict__ 
     const uint64_t i = t0 + uint64_t(k) * kBlock + threadIdx.x;
     if (i > st.nb) break;
     uint64_t xa, xb;
-    ef_values(st, p, bstart, off, i, xa, xb);
+    ef_values(st, p, rstart, off, i, xa, xb);
     const uint64_t rec = i * (p.low_a + p.low_b);
     or_bits(p.lower, rec, p.low_a ? (xa & ((1ull << p.low_a) - 1)) : 0, p.low_a);
     or_bits(p.lower, rec + p.low_a, p.low_b ? (xb & ((1ull << p.low_b) - 1)) : 0, p.low_b);
@@ -370,7 +384,7 @@ __global__ void __launch_bounds__(kBlock) k_ef_write(const DevSet* __restrict__ 
     if ((i & ((1u << kInvLo) - 1)) == 0) {
       const uint64_t a0 = (i >> kInvHi) << kInvHi;
       uint64_t ya, yb;
-      ef_values(st, p, bstart, off, a0, ya, yb);
+      ef_values(st, p, rstart, off, a0, ya, yb);
       const uint64_t da = pa - ((ya >> p.low_a) + a0), db = pb - ((yb >> p.low_b) + a0);
       p.subs[2 * (i >> kInvLo)] = static_cast<uint16_t>(da < 0xFFFF ? da : 0xFFFF);
       p.subs[2 * (i >> kInvLo) + 1] = static_cast<uint16_t>(db < 0xFFFF ? db : 0xFFFF);
@@ -497,17 +511,22 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   RS_CUDA(cudaGetDevice(&dev));
   RS_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
 
-  // ---- host plan: classes (distinct leaf sizes), bases, tilings
+  // ---- host plan: classes (distinct leaf sizes and leaf range extras), bases, tilings
   std::map<uint32_t, uint32_t> cls_of_leaf;
-  std::vector<uint32_t> class_leaf;
+  std::vector<uint32_t> class_leaf, class_extra;
+  bool any_extra = false;
   std::vector<DevSet> hs(count);
   uint64_t K = 0, NB = 0, key_tiles = 0, bucket_tiles = 0, elem_tiles = 0;
   for (uint32_t i = 0; i < count; i++) {
     const SetInput& si = in[i];
-    auto it = cls_of_leaf.find(si.leaf);
+    if (si.leaf_extra > 32 - si.leaf) return fail(RECSPLIT_E_INVALID, "leaf size + leaf range extra above 32");
+    any_extra |= si.leaf_extra != 0;
+    const uint32_t key = si.leaf | (si.leaf_extra << 8);
+    auto it = cls_of_leaf.find(key);
     if (it == cls_of_leaf.end()) {
-      it = cls_of_leaf.emplace(si.leaf, static_cast<uint32_t>(class_leaf.size())).first;
+      it = cls_of_leaf.emplace(key, static_cast<uint32_t>(class_leaf.size())).first;
       class_leaf.push_back(si.leaf);
+      class_extra.push_back(si.leaf_extra);
     }
     DevSet& d = hs[i];
     d.u64 = si.keys.u64;
@@ -582,7 +601,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   std::vector<uint64_t> tbase(nclass + 1, 0);
   std::string err;
   for (uint32_t c = 0; c < nclass; c++) {
-    if ((rc = build_tables(class_leaf[c], h_cls_max[c], &T[c], &err))) return fail(rc, err);
+    if ((rc = build_tables(class_leaf[c], class_extra[c], h_cls_max[c], &T[c], &err))) return fail(rc, err);
     tbase[c + 1] = tbase[c] + T[c].device_words.size();
   }
   auto table_mem = std::make_shared<DeviceMem>();
@@ -608,6 +627,18 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     count_launch();
   }
   if ((rc = exclusive_scan_u64(codes, cbase, NB, s))) return rc;
+  // prefix sums of the bucket output ranges: s_i itself unless a set has a
+  // leaf range extra
+  uint64_t* rstart = bstart;
+  if (any_extra) {
+    uint64_t* ranges;
+    if ((rc = sc.alloc(&ranges, NB + 1)) || (rc = sc.alloc(&rstart, NB + 1))) return rc;
+    if (NB) {
+      k_bucket_ranges<<<grid_for(NB), kBlock, 0, s>>>(counts, bset, d_sets, NB, ct, ranges);
+      count_launch();
+    }
+    if ((rc = exclusive_scan_u64(ranges, rstart, NB, s))) return rc;
+  }
 
   // grouping
   uint64_t* keys[2];
@@ -659,6 +690,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     for (uint32_t c = 0; c < nclass; c++) {
       a.table[c] = ct.t[c];
       a.leaf_of[c] = class_leaf[c];
+      a.extra_of[c] = class_extra[c];
       a.full_q[c] = q;
       q += full_cap[c];
       a.part_q[c] = q;
@@ -687,10 +719,10 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   }
 
   // A3 (split levels), A4 (leaves), A5 (lengths): optionally one CUDA graph
-  uint64_t *bits, *off, *set_T, *set_codes;
+  uint64_t *bits, *off, *set_T, *set_codes, *set_R;
   long long* set_db;
   if ((rc = sc.alloc(&bits, NB + 1)) || (rc = sc.alloc(&off, NB + 1)) || (rc = sc.alloc(&set_db, count)) ||
-      (rc = sc.alloc(&set_T, count)) || (rc = sc.alloc(&set_codes, count)))
+      (rc = sc.alloc(&set_T, count)) || (rc = sc.alloc(&set_codes, count)) || (rc = sc.alloc(&set_R, count)))
     return rc;
   // The graph is captured on a stream of its own (the caller's stream may be
   // the legacy default stream, which cannot be captured) and launched on s.
@@ -731,7 +763,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     if (!opt.use_graph) timer.mark();
     for (uint32_t c = 0; c < nclass; c++) {
       a.cls = c;
-      int r = launch_leaves(a, class_leaf[c], sm_count, ws);
+      int r = launch_leaves(a, class_leaf[c], class_extra[c], sm_count, ws);
       if (r) return r;
     }
     if (!opt.use_graph) timer.mark();
@@ -744,10 +776,10 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     if (r) return r;
     RS_CUDA(cudaMemsetAsync(set_db, 0x7F, count * sizeof(long long), ws));
     if (bucket_tiles) {
-      k_ef_prepare<<<static_cast<unsigned>(bucket_tiles), kBlock, 0, ws>>>(d_sets, count, bstart, off, set_db);
+      k_ef_prepare<<<static_cast<unsigned>(bucket_tiles), kBlock, 0, ws>>>(d_sets, count, rstart, off, set_db);
       count_launch();
     }
-    k_set_scalars<<<grid_for(count), kBlock, 0, ws>>>(d_sets, count, off, cbase, set_T, set_codes);
+    k_set_scalars<<<grid_for(count), kBlock, 0, ws>>>(d_sets, count, off, cbase, rstart, set_T, set_codes, set_R);
     count_launch();
     RS_CUDA(cudaGetLastError());
     return RECSPLIT_OK;
@@ -775,13 +807,14 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
 
   // sync 2: per-set tree size and minimum delta of the offsets list
   std::vector<long long> h_db(count);
-  std::vector<uint64_t> h_T(count), h_codes(count);
+  std::vector<uint64_t> h_T(count), h_codes(count), h_R(count);
   int herr = 0;
   // the deadline wait comes first: a copy into pageable host memory would
   // itself wait for the whole search
   if ((rc = wait_stream(s, d_error, timeout_ms(), t_call))) return rc;
   RS_CUDA(cudaMemcpyAsync(h_T.data(), set_T, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_codes.data(), set_codes, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  RS_CUDA(cudaMemcpyAsync(h_R.data(), set_R, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(h_db.data(), set_db, count * sizeof(long long), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaMemcpyAsync(&herr, d_error, sizeof(int), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaStreamSynchronize(s));
@@ -797,17 +830,20 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     const DevSet& d = hs[i];
     uint64_t* H = headers.data() + uint64_t(i) * kHeaderWords;
     const uint64_t n = d.n, nb = d.nb;
+    // the first list holds the prefix sums of the bucket output ranges (the
+    // bucket sizes unless the set has a leaf range extra); nr is their total
+    const uint64_t nr = h_R[i];
     const uint64_t T_bits = h_T[i];
-    const uint64_t beta = n ? ((T_bits / n) << 32) + (((T_bits % n) << 32) / n) : 0;
-    const int64_t delta_a = nb ? static_cast<int64_t>(h_set_min[i]) : 0;
+    const uint64_t beta = nr ? ((T_bits / nr) << 32) + (((T_bits % nr) << 32) / nr) : 0;
+    const int64_t delta_a = nb ? static_cast<int64_t>(T[d.cls].range[h_set_min[i]]) : 0;
     const int64_t delta_b = nb ? static_cast<int64_t>(h_db[i]) : 0;
-    const uint64_t xa_last = n - static_cast<uint64_t>(static_cast<int64_t>(nb) * delta_a);
-    const uint64_t z_last = T_bits - static_cast<uint64_t>((static_cast<unsigned __int128>(n) * beta) >> 32);
+    const uint64_t xa_last = nr - static_cast<uint64_t>(static_cast<int64_t>(nb) * delta_a);
+    const uint64_t z_last = T_bits - static_cast<uint64_t>((static_cast<unsigned __int128>(nr) * beta) >> 32);
     const uint64_t xb_last = static_cast<uint64_t>(static_cast<int64_t>(z_last) - static_cast<int64_t>(nb) * delta_b);
     const int la = ef_width(xa_last, nb + 1), lb = ef_width(xb_last, nb + 1);
     H[H_MAGIC] = kMagic;
     H[H_N] = n;
-    H[H_LEAF] = d.leaf;
+    H[H_LEAF] = d.leaf | (static_cast<uint64_t>(class_extra[d.cls]) << 8);
     H[H_BUCKET] = in[i].bucket_size;
     H[H_NB] = nb;
     H[H_TBITS] = T_bits;
@@ -860,7 +896,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     k_write_codes<<<grid_for(NB), kBlock, 0, s>>>(counts, cbase, seeds, sizes, bset, d_sets, d_outs, ct, off, NB);
     count_launch();
   }
-  k_ef_write<<<static_cast<unsigned>(elem_tiles), kBlock, 0, s>>>(d_sets, count, d_outs, bstart, off);
+  k_ef_write<<<static_cast<unsigned>(elem_tiles), kBlock, 0, s>>>(d_sets, count, d_outs, rstart, off);
   count_launch();
   timer.mark();
   unsigned long long* work = nullptr;
@@ -889,6 +925,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     h->d_blob = d_arena + blob_off[i];
     h->d_table = const_cast<uint64_t*>(ct.t[hs[i].cls]);
     h->ncodes = h->header[H_CODES];
+    h->range_size = h_R[i];
     h->device = dev;
     out[i] = h;
   }

@@ -27,6 +27,11 @@ enum HeaderWord : int {
   H_DELTA_A, H_DELTA_B, H_LOW_A, H_LOW_B, H_UP_A, H_UP_B, H_WORDS, H_CODES
 };
 
+// Header word H_LEAF holds the leaf size in bits 0..7 and the leaf range
+// extra of the perfect, non-minimal variant in bits 8..15 (0: minimal).
+inline uint32_t header_leaf(const uint64_t* H) { return static_cast<uint32_t>(H[H_LEAF] & 0xFF); }
+inline uint32_t header_extra(const uint64_t* H) { return static_cast<uint32_t>((H[H_LEAF] >> 8) & 0xFF); }
+
 inline uint64_t words_of_bits(uint64_t bits) { return (bits + 63) >> 6; }
 
 // Word offsets of the sections of a structure, derived from its header.
@@ -43,6 +48,7 @@ struct Strategy {
   uint32_t leaf;
   uint64_t lower;  // s * leaf
   uint64_t upper;  // s * t * leaf
+  uint32_t extra = 0;  // leaf range extra e: a leaf of m >= 2 keys maps into [0, m + e)
 };
 Strategy make_strategy(uint32_t leaf);
 
@@ -67,9 +73,13 @@ struct Tables {
   std::vector<uint64_t> fixed_bits;
   std::vector<uint64_t> codes;
   std::vector<uint64_t> expected_trials;  // 1/p rounded up (search stall detection)
+  std::vector<uint64_t> range;            // output range of a subtree (m when extra = 0)
   std::vector<uint64_t> device_words;     // kTableWords per size
 };
-int build_tables(uint32_t leaf, uint64_t mmax, Tables* out, std::string* err);
+// Device words per node size m: w0 = subtree fixed bits | subtree codes << 32;
+// w1 = unit | fanout << 32 | r << 40; w2 = expected trials;
+// w3 = ceil(2^32 / unit) | subtree output range << 32.
+int build_tables(uint32_t leaf, uint32_t extra, uint64_t mmax, Tables* out, std::string* err);
 
 // ---------------------------------------------------------------- handle
 // Device memory released when the last structure that uses it is freed
@@ -81,6 +91,7 @@ struct DeviceMem {
 
 struct Handle {
   uint64_t header[kHeaderWords];
+  uint64_t range_size = 0;  // lookups of member keys fall in [0, range_size) (n when leaf extra is 0)
   Layout layout;
   std::shared_ptr<DeviceMem> blob_mem, table_mem;
   uint64_t* d_blob = nullptr;   // serialized structure, device resident
@@ -99,6 +110,8 @@ struct View {
   const uint16_t* subs;
   const uint64_t* table;  // kTableWords words per size
   const uint64_t* so;  // s_i, o_i of every bucket decoded beforehand, or null
+  uint64_t mmax;       // largest bucket (the tables cover sizes 0 .. mmax)
+  uint32_t extra;      // leaf range extra (0: minimal)
   uint64_t nb;
   uint64_t beta;
   int64_t delta_a, delta_b;
@@ -158,6 +171,7 @@ struct SetInput {
   KeyInput keys;
   uint32_t leaf = 0;
   uint32_t bucket_size = 0;
+  uint32_t leaf_extra = 0;  // > 0: perfect, non-minimal variant (leaf ranges m + leaf_extra)
 };
 
 struct BuildOptions {
@@ -209,10 +223,11 @@ struct SearchArgs {
   uint32_t* work_counter;                 // dynamic scheduling counter (zeroed per launch)
   int* error;                             // first error code
   uint32_t cls;                           // class of a leaf launch
+  uint32_t extra_of[kMaxClasses];         // leaf range extra per class
 };
 
 int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s);
-int launch_leaves(const SearchArgs& a, uint32_t leaf, int sm_count, cudaStream_t s);
+int launch_leaves(const SearchArgs& a, uint32_t leaf, uint32_t extra, int sm_count, cudaStream_t s);
 
 // Launch shapes of the searches for one leaf size (see recsplit_tuning_t).
 recsplit_tuning_t tuning_for(uint32_t leaf);

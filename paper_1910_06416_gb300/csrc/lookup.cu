@@ -29,8 +29,34 @@ __device__ __forceinline__ uint64_t ef_offset(const View& v, uint64_t b, uint64_
   return static_cast<uint64_t>(z + static_cast<int64_t>(bs));
 }
 
+// RANGE: the structure has a leaf range extra (perfect, non-minimal
+// variant); false compiles the minimal structure's path alone.
+template <bool RANGE>
 __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
 
+// Output range of a subtree of m keys (table word 3, upper half).
+__device__ __forceinline__ uint64_t node_range(const View& v, uint64_t m) {
+  return __ldg(v.table + kTableWords * m + 3) >> 32;
+}
+
+// The bucket size whose output range is R.  Without a leaf range extra the
+// range is the size; with one, ranges grow strictly with the size (the tables
+// are built only then), so a binary search over sizes 0 .. mmax finds it.
+template <bool RANGE>
+__device__ __forceinline__ uint32_t size_of_range(const View& v, uint64_t R) {
+  if (!RANGE || v.extra == 0) return static_cast<uint32_t>(R);
+  uint64_t a = 0, b = v.mmax;
+  while (a < b) {
+    const uint64_t mid = (a + b + 1) >> 1;
+    if (node_range(v, mid) <= R)
+      a = mid;
+    else
+      b = mid - 1;
+  }
+  return static_cast<uint32_t>(a);
+}
+
+template <bool RANGE>
 __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint64_t lo) {
   if (v.nb == 0) return 0;
   const uint64_t b = bucket_of(hi, v.nb);
@@ -42,22 +68,23 @@ __device__ __forceinline__ uint64_t lookup_one(const View& v, uint64_t hi, uint6
   const uint64_t xa1 = ((pa1 - b - 1) << v.low_a) | read_bits(v.lower, rec + rec_w, v.low_a);
   const uint64_t s0 = xa0 + static_cast<uint64_t>(static_cast<int64_t>(b) * v.delta_a);
   const uint64_t s1 = xa1 + static_cast<uint64_t>(static_cast<int64_t>(b + 1) * v.delta_a);
-  const uint32_t m = static_cast<uint32_t>(s1 - s0);
+  const uint32_t m = size_of_range<RANGE>(v, s1 - s0);
   if (m <= 1) return s0;
-  return descend(v, s0, m, ef_offset(v, b, s0), lo);
+  return descend<RANGE>(v, s0, m, ef_offset(v, b, s0), lo);
 }
 
 // The same lookup with s_i, o_i of every bucket decoded beforehand (so[2i],
 // so[2i+1]; so[2N] = n): for batches with more queries than buckets.
+template <bool RANGE>
 __device__ __forceinline__ uint64_t lookup_decoded(const View& v, const uint64_t* __restrict__ so, uint64_t hi,
                                                    uint64_t lo) {
   if (v.nb == 0) return 0;
   const uint64_t b = bucket_of(hi, v.nb);
   const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(so) + b);
   const uint64_t s1 = __ldg(so + 2 * b + 2);
-  const uint32_t m = static_cast<uint32_t>(s1 - p.x);
+  const uint32_t m = size_of_range<RANGE>(v, s1 - p.x);
   if (m <= 1) return p.x;
-  return descend(v, p.x, m, p.y, lo);
+  return descend<RANGE>(v, p.x, m, p.y, lo);
 }
 
 // Bit reads inside one bucket's code.  The tree bits are read as 32-bit
@@ -109,7 +136,9 @@ __device__ __forceinline__ uint32_t code_select(const uint32_t* __restrict__ t, 
 
 // Sec. 4 / 6.2: descent of the splitting tree of a bucket of m keys whose
 // code starts at bit o.
+template <bool RANGE>
 __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
+  const uint32_t extra = RANGE ? v.extra : 0;
   const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
   uint32_t fixed = static_cast<uint32_t>(o & 31);
   uint32_t c = 0;
@@ -127,8 +156,8 @@ __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t
     const uint32_t one = code_next_one(t, unary);
     const uint64_t seed = (uint64_t(one - unary) << r) | low;
     unary = one + 1;
+    if (fanout == 0) return s0 + c + phi_pre(xpre, family_key(seed, depth), m + extra);
     const uint32_t val = phi_pre(xpre, family_key(seed, depth), m);
-    if (fanout == 0) return s0 + c + val;
     const uint32_t magic = static_cast<uint32_t>(__ldg(v.table + kTableWords * m + 3));
     const uint32_t part = min(magic ? __umulhi(val, magic) : val / unit, fanout - 1);
     const uint32_t next = part + 1 < fanout ? unit : m - unit * (fanout - 1);
@@ -138,7 +167,8 @@ __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t
       fixed += part * static_cast<uint32_t>(tu.x);
       const uint32_t skip = part * static_cast<uint32_t>(tu.x >> 32);
       if (skip) unary = code_select(t, unary, skip - 1) + 1;
-      c += part * unit;
+      // keys (or, with a leaf range extra, output ranges) of the siblings left behind
+      c += extra ? static_cast<uint32_t>(part * node_range(v, unit)) : part * unit;
     }
     m = next;
     tw = tn;
@@ -155,15 +185,17 @@ __global__ void k_ef_decode(View v, uint64_t* __restrict__ so) {
   }
 }
 
+template <bool RANGE>
 __global__ void k_lookup_u64(View v, const uint64_t* __restrict__ so, const uint64_t* __restrict__ keys, uint64_t q,
                              uint64_t* __restrict__ out) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t hi, lo;
     signature_u64(__ldg(keys + i), hi, lo);
-    out[i] = so ? lookup_decoded(v, so, hi, lo) : lookup_one(v, hi, lo);
+    out[i] = so ? lookup_decoded<RANGE>(v, so, hi, lo) : lookup_one<RANGE>(v, hi, lo);
   }
 }
 
+template <bool RANGE>
 __global__ void k_lookup_bytes(View v, const uint64_t* __restrict__ so, const uint8_t* __restrict__ bytes,
                                const uint64_t* __restrict__ offsets, uint64_t q, uint64_t* __restrict__ out) {
   const uint64_t last = __ldg(offsets + q);  // the bytes span [0, offsets[q])
@@ -172,7 +204,7 @@ __global__ void k_lookup_bytes(View v, const uint64_t* __restrict__ so, const ui
     uint64_t hi, lo;
     const bool ok = o0 <= o1 && o1 <= last;  // else read as the empty string
     signature_bytes(bytes + (ok ? o0 : 0), ok ? o1 - o0 : 0, hi, lo);
-    out[i] = so ? lookup_decoded(v, so, hi, lo) : lookup_one(v, hi, lo);
+    out[i] = so ? lookup_decoded<RANGE>(v, so, hi, lo) : lookup_one<RANGE>(v, hi, lo);
   }
 }
 
@@ -201,7 +233,8 @@ __global__ void k_lookup_many(const View* __restrict__ views, const uint32_t* __
     uint64_t hi, lo;
     signature_u64(__ldg(keys + i), hi, lo);
     const View& v = views[__ldg(ids + i)];
-    out[i] = v.so ? lookup_decoded(v, v.so, hi, lo) : lookup_one(v, hi, lo);
+    out[i] = v.extra ? (v.so ? lookup_decoded<true>(v, v.so, hi, lo) : lookup_one<true>(v, hi, lo))
+                     : (v.so ? lookup_decoded<false>(v, v.so, hi, lo) : lookup_one<false>(v, hi, lo));
   }
 }
 
@@ -215,7 +248,8 @@ __global__ void k_lookup_many_bytes(const View* __restrict__ views, const uint32
     const bool ok = o0 <= o1 && o1 <= last;  // else read as the empty string
     signature_bytes(bytes + (ok ? o0 : 0), ok ? o1 - o0 : 0, hi, lo);
     const View& v = views[__ldg(ids + i)];
-    out[i] = v.so ? lookup_decoded(v, v.so, hi, lo) : lookup_one(v, hi, lo);
+    out[i] = v.extra ? (v.so ? lookup_decoded<true>(v, v.so, hi, lo) : lookup_one<true>(v, hi, lo))
+                     : (v.so ? lookup_decoded<false>(v, v.so, hi, lo) : lookup_one<false>(v, hi, lo));
   }
 }
 
@@ -302,6 +336,8 @@ int decode_views(View* views, uint32_t count, uint64_t q, cudaStream_t s, uint64
 View make_view(const Handle& h) {
   View v;
   v.so = nullptr;
+  v.mmax = h.header[H_MMAX];
+  v.extra = header_extra(h.header);
   const uint64_t* H = h.header;
   v.tree = h.d_blob + h.layout.tree;
   v.lower = h.d_blob + h.layout.lower;
@@ -316,7 +352,7 @@ View make_view(const Handle& h) {
   v.delta_b = static_cast<int64_t>(H[H_DELTA_B]);
   v.low_a = static_cast<uint32_t>(H[H_LOW_A]);
   v.low_b = static_cast<uint32_t>(H[H_LOW_B]);
-  v.leaf = static_cast<uint32_t>(H[H_LEAF]);
+  v.leaf = header_leaf(H);
   return v;
 }
 
@@ -342,9 +378,10 @@ int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaSt
     so = nullptr;
   }
   if (q.u64)
-    k_lookup_u64<<<grid, block, 0, s>>>(v, so, q.u64, q.n, d_out);
+    (v.extra ? k_lookup_u64<true> : k_lookup_u64<false>)<<<grid, block, 0, s>>>(v, so, q.u64, q.n, d_out);
   else
-    k_lookup_bytes<<<grid, block, 0, s>>>(v, so, q.bytes, q.offsets, q.n, d_out);
+    (v.extra ? k_lookup_bytes<true> : k_lookup_bytes<false>)<<<grid, block, 0, s>>>(v, so, q.bytes, q.offsets, q.n,
+                                                                                    d_out);
   count_launch();
   const cudaError_t e = cudaGetLastError();
   if (so) cudaFreeAsync(so, s);

@@ -404,9 +404,25 @@ __device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const
 // Blocks per SM the register budget must allow (keys live in registers).
 __host__ __device__ constexpr int leaf_min_blocks(int l) { return l <= 5 ? 5 : (l <= 12 ? 4 : 3); }
 
-template <int LMAX, bool FULL, bool TWO>
+// Leaf of m <= LMAX keys of the perfect, non-minimal variant: the values in
+// [0, m + extra) must be distinct, i.e. the sum of the kept one-hot values
+// must have m one bits (a sum of powers of two loses one bits on every
+// carry, and a carry out of bit 31 only lowers the count further).
+template <int LMAX>
+__device__ __forceinline__ bool leaf_trial_range(const uint64_t (&x)[LMAX], const uint32_t (&keep)[LMAX], uint32_t m,
+                                                 uint32_t range, uint64_t kp) {
+  uint32_t seen = 0;
+#pragma unroll
+  for (int j = 0; j < LMAX; j++) seen += (1u << phi_pre(x[j], kp, range)) & keep[j];
+  return static_cast<uint32_t>(__popc(seen)) == m;
+}
+
+// RANGE: perfect, non-minimal variant (leaf range m + extra of the class);
+// the queue is then the class's full leaves if qfull, else its partial ones.
+template <int LMAX, bool FULL, bool TWO, bool RANGE = false>
 __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(SearchArgs a, uint32_t gwarps,
-                                                                            uint32_t chunk, uint32_t spl) {
+                                                                            uint32_t chunk, uint32_t spl,
+                                                                            uint32_t qfull) {
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
   constexpr bool kTwoPhase = FULL && TWO && LMAX >= 4;
@@ -414,8 +430,10 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t gid = warp / gwarps, wig = warp % gwarps;
   const bool leader = wig == 0 && lane == 0;
-  const Node* queue = FULL ? a.full_q[a.cls] : a.part_q[a.cls];
-  const uint32_t total = FULL ? a.full_n[a.cls] : a.part_n[a.cls];
+  const bool from_full = FULL || (RANGE && qfull);
+  const Node* queue = from_full ? a.full_q[a.cls] : a.part_q[a.cls];
+  const uint32_t total = from_full ? a.full_n[a.cls] : a.part_n[a.cls];
+  const uint32_t extra = RANGE ? a.extra_of[a.cls] : 0;
   const uint64_t* table = a.table[a.cls];
 
   for (;;) {
@@ -478,7 +496,9 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
         } else {
           for (uint32_t j = 0; j < spl; j++) {
             const uint64_t kp = family_key(base + j * 32 + lane, depth);
-            const bool ok = FULL ? leaf_trial_full<LMAX>(x, kp) : leaf_trial_part<LMAX>(x, keep, m, kp);
+            const bool ok = RANGE  ? leaf_trial_range<LMAX>(x, keep, m, m + extra, kp)
+                            : FULL ? leaf_trial_full<LMAX>(x, kp)
+                                   : leaf_trial_part<LMAX>(x, keep, m, kp);
             const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
             if (hits && found == ~0ull) found = base + j * 32 + __ffs(hits) - 1;
           }
@@ -507,14 +527,15 @@ int persistent_grid(K kernel, size_t smem, int sm_count, int* blocks) {
   return RECSPLIT_OK;
 }
 
-template <int LMAX, bool FULL, bool TWO = false>
-int launch_leaf_kernel(const SearchArgs& a, const recsplit_tuning_t& t, int sm_count, cudaStream_t s) {
-  auto kern = k_leaves<LMAX, FULL, TWO>;
+template <int LMAX, bool FULL, bool TWO = false, bool RANGE = false>
+int launch_leaf_kernel(const SearchArgs& a, const recsplit_tuning_t& t, int sm_count, cudaStream_t s,
+                       uint32_t qfull = 0) {
+  auto kern = k_leaves<LMAX, FULL, TWO, RANGE>;
   int blocks = 0;
   int rc = persistent_grid(kern, 0, sm_count, &blocks);
   if (rc) return rc;
   RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
-  kern<<<blocks, kThreads, 0, s>>>(a, t.leaf_warps, t.leaf_chunk, t.leaf_seeds_per_lane);
+  kern<<<blocks, kThreads, 0, s>>>(a, t.leaf_warps, t.leaf_chunk, t.leaf_seeds_per_lane, qfull);
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;
@@ -587,9 +608,20 @@ int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, i
   return RECSPLIT_OK;
 }
 
-int launch_leaves(const SearchArgs& a, uint32_t leaf, int sm_count, cudaStream_t s) {
+int launch_leaves(const SearchArgs& a, uint32_t leaf, uint32_t extra, int sm_count, cudaStream_t s) {
   if (leaf < 2) return RECSPLIT_OK;
   const recsplit_tuning_t t = tuning_for(leaf);
+  if (extra) {
+    // perfect, non-minimal variant: the full and the partial leaves, each
+    // searched over [0, m + extra) by the kernel for leaves of up to LMAX keys
+    for (uint32_t qfull : {1u, 0u}) {
+      const int rc = leaf <= 8    ? launch_leaf_kernel<8, false, false, true>(a, t, sm_count, s, qfull)
+                     : leaf <= 16 ? launch_leaf_kernel<16, false, false, true>(a, t, sm_count, s, qfull)
+                                  : launch_leaf_kernel<24, false, false, true>(a, t, sm_count, s, qfull);
+      if (rc) return rc;
+    }
+    return RECSPLIT_OK;
+  }
   int rc = kFull[leaf](a, t, sm_count, s);
   if (rc) return rc;
   if (leaf == 2) return RECSPLIT_OK;  // no leaves between 2 and leaf - 1

@@ -49,12 +49,17 @@ static int floor_log2(uint64_t x) { return x ? 63 - __builtin_clzll(x) : 0; }
 
 // ln of the probability that one trial succeeds at a node of m keys:
 // m!/m^m for a leaf (Sec. 5.2); for a split Eq. probsplit, i.e. that times
-// k^k/k! for every part k (Sec. 5.1).
+// k^k/k! for every part k (Sec. 5.1).  With leaf range extra e a leaf trial
+// succeeds when its m values are distinct in [0, R), R = m + e:
+// R! / ((R - m)! R^m) (m!/m^m for e = 0).
 static double log_trial_success(const Strategy& st, uint64_t m) {
   const double dm = static_cast<double>(m);
-  double v = std::lgamma(dm + 1.0) - dm * std::log(dm);
   const Shape sh = shape_of(st, m);
-  if (sh.fanout == 0) return v;
+  if (sh.fanout == 0) {
+    const double dr = static_cast<double>(m + st.extra);
+    return std::lgamma(dr + 1.0) - std::lgamma(dr - dm + 1.0) - dm * std::log(dr);
+  }
+  double v = std::lgamma(dm + 1.0) - dm * std::log(dm);
   auto term = [](uint64_t k) {
     const double dk = static_cast<double>(k);
     return dk * std::log(dk) - std::lgamma(dk + 1.0);
@@ -83,15 +88,20 @@ int golomb_rice_param(const Strategy& st, uint64_t m) {
   return v > 0 ? static_cast<int>(v >> 1) : 0;
 }
 
-int build_tables(uint32_t leaf, uint64_t mmax, Tables* T, std::string* err) {
-  const Strategy st = make_strategy(leaf);
+int build_tables(uint32_t leaf, uint32_t extra, uint64_t mmax, Tables* T, std::string* err) {
+  Strategy st = make_strategy(leaf);
+  st.extra = extra;
   if (mmax < 2) mmax = 2;
   T->mmax = mmax;
   T->r.assign(mmax + 1, 0);
   T->fixed_bits.assign(mmax + 1, 0);
   T->codes.assign(mmax + 1, 0);
   T->expected_trials.assign(mmax + 1, 0);
+  T->range.assign(mmax + 1, 0);
   T->device_words.assign(kTableWords * (mmax + 1), 0);
+  // sizes 0 and 1: no code, output range m
+  T->range[1] = 1;
+  T->device_words[kTableWords * 1 + 3] = uint64_t(1) << 32;
   for (uint64_t m = 2; m <= mmax; m++) {
     const Shape sh = shape_of(st, m);
     const int r = golomb_rice_param(st, m);
@@ -103,6 +113,13 @@ int build_tables(uint32_t leaf, uint64_t mmax, Tables* T, std::string* err) {
     T->r[m] = static_cast<uint8_t>(r);
     T->fixed_bits[m] = fb;
     T->codes[m] = nc;
+    T->range[m] = sh.fanout ? (sh.fanout - 1) * T->range[sh.unit] + T->range[sh.last] : m + extra;
+    // a bucket's size is read back from its output range: the range must
+    // grow strictly with the size (checked for every size)
+    if (T->range[m] <= T->range[m - 1] || T->range[m] >= (1ull << 32)) {
+      if (err) *err = "subtree output ranges do not grow with the node size";
+      return RECSPLIT_E_INVALID;
+    }
     const double et = std::exp(-log_trial_success(st, m));
     T->expected_trials[m] = et > 1e18 ? ~0ull : static_cast<uint64_t>(std::ceil(et));
     if (fb >= (1ull << 32) || nc >= (1ull << 32) || r >= 32 || sh.unit >= (1ull << 32)) {
@@ -113,13 +130,22 @@ int build_tables(uint32_t leaf, uint64_t mmax, Tables* T, std::string* err) {
     T->device_words[kTableWords * m + 1] =
         sh.unit | (static_cast<uint64_t>(sh.fanout) << 32) | (static_cast<uint64_t>(r) << 40);
     T->device_words[kTableWords * m + 2] = T->expected_trials[m];
-    T->device_words[kTableWords * m + 3] = sh.unit >= 2 ? ((1ull << 32) + sh.unit - 1) / sh.unit : 0;
+    T->device_words[kTableWords * m + 3] =
+        (sh.unit >= 2 ? ((1ull << 32) + sh.unit - 1) / sh.unit : 0) | (T->range[m] << 32);
   }
-  // sizes 0 and 1: leaves without a code
   return RECSPLIT_OK;
 }
 
 }  // namespace rs
+
+extern "C" int recsplit_golomb_rice_params_extra(uint32_t leaf_size, uint32_t leaf_extra, uint64_t m_hi,
+                                                 uint8_t* out) {
+  if (leaf_size < 1 || leaf_size > rs::kMaxLeaf || leaf_size + leaf_extra > 32 || !out) return RECSPLIT_E_INVALID;
+  rs::Strategy st = rs::make_strategy(leaf_size);
+  st.extra = leaf_extra;
+  for (uint64_t m = 0; m <= m_hi; m++) out[m] = static_cast<uint8_t>(rs::golomb_rice_param(st, m));
+  return RECSPLIT_OK;
+}
 
 extern "C" int recsplit_golomb_rice_params(uint32_t leaf_size, uint64_t m_hi, uint8_t* out) {
   if (leaf_size < 1 || leaf_size > rs::kMaxLeaf || !out) return RECSPLIT_E_INVALID;

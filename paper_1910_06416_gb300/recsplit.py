@@ -30,7 +30,8 @@ class Stats(C.Structure):
     _fields_ = [("n", C.c_uint64), ("leaf_size", C.c_uint32), ("bucket_size", C.c_uint32),
                 ("num_buckets", C.c_uint64), ("tree_bits", C.c_uint64), ("total_bits", C.c_uint64),
                 ("max_bucket", C.c_uint64), ("num_codes", C.c_uint64), ("tree_bits_per_key", C.c_double),
-                ("bits_per_key", C.c_double)]
+                ("bits_per_key", C.c_double), ("leaf_extra", C.c_uint32), ("reserved", C.c_uint32),
+                ("range_size", C.c_uint64)]
 
 
 class Profile(C.Structure):
@@ -93,6 +94,8 @@ def lib():
             L.recsplit_build_u64.argtypes = [p, u64, u32, u32, p, C.POINTER(p)]
             L.recsplit_build.argtypes = [p, u64, u32, u32, p, C.POINTER(p)]
             L.recsplit_build_bytes.argtypes = [p, p, u64, u32, u32, p, C.POINTER(p)]
+            L.recsplit_build_perfect_u64.argtypes = [p, u64, u32, u32, u32, p, C.POINTER(p)]
+            L.recsplit_build_perfect_bytes.argtypes = [p, p, u64, u32, u32, u32, p, C.POINTER(p)]
             L.recsplit_lookup_u64.argtypes = [p, p, u64, p, p]
             L.recsplit_lookup.argtypes = [p, p, u64, p, p]
             L.recsplit_lookup_bytes.argtypes = [p, p, p, u64, p, p]
@@ -106,6 +109,7 @@ def lib():
             L.recsplit_last_error.argtypes = []
             L.recsplit_last_error.restype = C.c_char_p
             L.recsplit_golomb_rice_params.argtypes = [u32, u64, p]
+            L.recsplit_golomb_rice_params_extra.argtypes = [u32, u32, u64, p]
             L.recsplit_set_profiling.argtypes = [i]
             L.recsplit_last_profile.argtypes = [C.POINTER(Profile)]
             L.recsplit_lookup_u64_static.argtypes = [p, p, u64, p, p]
@@ -200,6 +204,23 @@ def recsplit_build_bytes(data, offsets, leaf_size: int, bucket_size: int, stream
     h = C.c_void_p()
     _check(lib().recsplit_build_bytes(_ptr(data), _ptr(offsets), _count(offsets) - 1, leaf_size, bucket_size,
                                       _stream(stream), C.byref(h)), "recsplit_build_bytes")
+    return h.value
+
+
+def recsplit_build_perfect_u64(keys, leaf_size: int, bucket_size: int, leaf_extra: int, stream=None) -> int:
+    """Perfect, non-minimal variant: leaves of m keys map into m + leaf_extra values."""
+    h = C.c_void_p()
+    _check(lib().recsplit_build_perfect_u64(_ptr(keys), _count(keys), leaf_size, bucket_size, leaf_extra,
+                                            _stream(stream), C.byref(h)), "recsplit_build_perfect_u64")
+    return h.value
+
+
+def recsplit_build_perfect_bytes(data, offsets, leaf_size: int, bucket_size: int, leaf_extra: int,
+                                 stream=None) -> int:
+    h = C.c_void_p()
+    _check(lib().recsplit_build_perfect_bytes(_ptr(data), _ptr(offsets), _count(offsets) - 1, leaf_size,
+                                              bucket_size, leaf_extra, _stream(stream), C.byref(h)),
+           "recsplit_build_perfect_bytes")
     return h.value
 
 
@@ -389,6 +410,13 @@ def recsplit_golomb_rice_params(leaf_size: int, m_hi: int) -> np.ndarray:
     return out
 
 
+def recsplit_golomb_rice_params_extra(leaf_size: int, leaf_extra: int, m_hi: int) -> np.ndarray:
+    out = np.zeros(m_hi + 1, dtype=np.uint8)
+    _check(lib().recsplit_golomb_rice_params_extra(leaf_size, leaf_extra, m_hi, _ptr(out)),
+           "recsplit_golomb_rice_params_extra")
+    return out
+
+
 def recsplit_set_profiling(enabled: bool) -> None:
     _check(lib().recsplit_set_profiling(1 if enabled else 0), "recsplit_set_profiling")
 
@@ -417,6 +445,16 @@ class Structure:
     @classmethod
     def build_bytes(cls, data, offsets, leaf_size: int, bucket_size: int, stream=None) -> "Structure":
         return cls(recsplit_build_bytes(data, offsets, leaf_size, bucket_size, stream))
+
+    @classmethod
+    def build_perfect_u64(cls, keys, leaf_size: int, bucket_size: int, leaf_extra: int,
+                          stream=None) -> "Structure":
+        return cls(recsplit_build_perfect_u64(keys, leaf_size, bucket_size, leaf_extra, stream))
+
+    @classmethod
+    def build_perfect_bytes(cls, data, offsets, leaf_size: int, bucket_size: int, leaf_extra: int,
+                            stream=None) -> "Structure":
+        return cls(recsplit_build_perfect_bytes(data, offsets, leaf_size, bucket_size, leaf_extra, stream))
 
     @classmethod
     def deserialize(cls, words, stream=None) -> "Structure":

@@ -61,6 +61,24 @@ def test_golomb_rice_table_equals_oracle(rs, orc):
         assert [int(got[m]) for m in ms] == [orc.golomb_rice(leaf, m) for m in ms]
 
 
+def test_golomb_rice_table_with_leaf_extra_equals_oracle(rs, orc):
+    """The same for the perfect, non-minimal variant (leaf ranges m + e)."""
+    for leaf, extra in [(2, 1), (5, 1), (8, 2), (8, 8), (12, 4), (16, 16), (24, 8)]:
+        got = rs.recsplit_golomb_rice_params_extra(leaf, extra, 3000)
+        want = np.array([orc.golomb_rice(leaf, m, extra=extra) for m in range(3001)], dtype=np.uint8)
+        assert np.array_equal(got, want), (leaf, extra)
+    assert np.array_equal(rs.recsplit_golomb_rice_params_extra(8, 0, 500), rs.recsplit_golomb_rice_params(8, 500))
+    with pytest.raises(rs.RecSplitError):
+        rs.recsplit_golomb_rice_params_extra(24, 9, 10)  # leaf + extra above 32
+
+
+def test_perfect_build_arguments_rejected_before_device_work(rs):
+    keys = np.arange(10, dtype=np.uint64)
+    with pytest.raises(rs.RecSplitError) as e:
+        rs.recsplit_build_perfect_u64(keys, 24, 5, 9)
+    assert e.value.code == rs.E_INVALID
+
+
 def test_tuning_shapes_are_validated(rs):
     t = rs.recsplit_get_tuning(8)
     assert t["leaf_warps"] in (1, 2, 4, 8)
