@@ -134,6 +134,19 @@ bool on_device(const void* p) {
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (cudaHostAlloc, cudaHostRegister,
+// a pinned torch tensor), or null for other memory.  The GPU reads such
+// memory directly over the host link, so a build that reads its keys once
+// takes them from there instead of staging a copy first.
+void* pinned_device_alias(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
+}
+
 // Device copy of a host buffer (or the device pointer itself).
 struct Staged {
   void* dev = nullptr;
@@ -183,7 +196,11 @@ static int build_u64_impl(const uint64_t* keys, uint64_t n, uint32_t leaf_size, 
   if (n && !keys) return fail(RECSPLIT_E_INVALID, "keys is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Staged k;
-  if ((rc = k.from(keys, n * sizeof(uint64_t), n && on_device(keys), s))) return rc;
+  void* alias = n && !on_device(keys) ? pinned_device_alias(keys) : nullptr;
+  if (alias)
+    k.dev = alias;  // read once by the signature kernel: no staging copy
+  else if ((rc = k.from(keys, n * sizeof(uint64_t), n && on_device(keys), s)))
+    return rc;
   SetInput in;
   in.keys.u64 = static_cast<const uint64_t*>(k.dev);
   in.keys.n = n;
@@ -226,8 +243,15 @@ static int build_bytes_impl(const uint8_t* bytes, const uint64_t* offsets, uint6
     // do not decrease
     if (offsets[n] < offsets[0]) return fail(RECSPLIT_E_INVALID, "byte-string offsets must not decrease");
     const uint64_t total = offsets[n];
-    if ((rc = b.from(bytes, total, false, s)) || (rc = o.from(offsets, (n + 1) * sizeof(uint64_t), false, s)))
+    void* ab = pinned_device_alias(bytes);
+    void* ao = pinned_device_alias(offsets);
+    if (ab && ao) {
+      b.dev = ab;  // read once by the signature kernel: no staging copy
+      o.dev = ao;
+    } else if ((rc = b.from(bytes, total, false, s)) ||
+               (rc = o.from(offsets, (n + 1) * sizeof(uint64_t), false, s))) {
       return rc;
+    }
   } else {
     b.dev = const_cast<uint8_t*>(bytes);
     o.dev = const_cast<uint64_t*>(offsets);

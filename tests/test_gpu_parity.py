@@ -119,6 +119,24 @@ def test_host_buffers_give_the_same_structure(rs, orc):
     assert_same_blob(sb.serialize(), orc.build_bytes(bk.data, bk.offsets, 8, 100))
 
 
+def test_pinned_host_buffers_are_read_in_place(rs, orc):
+    # page-locked host keys are read by the signature kernel directly
+    keys = inputs.u64_keys(60000, 29)
+    pinned = torch.from_numpy(keys.view(np.int64)).pin_memory()
+    s = rs.Structure.build_u64(pinned, 8, 100)
+    assert_same_blob(s.serialize(), orc.build_u64(keys, 8, 100))
+    bk = inputs.byte_keys(30000, 30)
+    pd = torch.from_numpy(bk.data.copy()).pin_memory()
+    po = torch.from_numpy(bk.offsets.astype(np.uint64).view(np.int64)).pin_memory()
+    sb = rs.Structure.build_bytes(pd, po, 8, 100)
+    assert_same_blob(sb.serialize(), orc.build_bytes(bk.data, bk.offsets, 8, 100))
+    bad = bk.offsets.astype(np.uint64).copy()
+    bad[11] = bad[10] - 1
+    with pytest.raises(rs.RecSplitError) as e:
+        rs.Structure.build_bytes(pd, torch.from_numpy(bad.view(np.int64)).pin_memory(), 8, 100)
+    assert e.value.code == rs.E_INVALID
+
+
 def test_serialize_round_trip(rs, orc):
     keys = inputs.u64_keys(40000, 23)
     s = gpu_build_u64(rs, keys, 5, 5)
