@@ -150,7 +150,9 @@ int recsplit_lookup(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint6
  * otherwise cap must be at least that size.  Synchronises with the device. */
 int recsplit_serialize(const recsplit_t* h, void* buf, size_t cap, size_t* len);
 
-/* Structure from a serialized buffer in host memory (copied). */
+/* Structure from a serialized buffer in host memory (copied).  The header
+ * and the section sizes are checked (RECSPLIT_E_INVALID); the codes are not,
+ * so load only buffers written by recsplit_serialize. */
 int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t** out);
 
 /* Summary figures of a structure (host only, no device work). */
