@@ -33,7 +33,9 @@ __device__ __forceinline__ void signature_u64(uint64_t key, uint64_t& hi, uint64
 // swapped, then the length folded into both.  The string is read with
 // aligned 4-byte loads of the words that hold at least one of its bytes (no
 // load leaves the page that holds the string); each 8-byte word is two funnel
-// shifts of three consecutive loaded words.
+// shifts of three consecutive loaded words.  One loop covers every 8-byte
+// word including the zero-padded last one, so the lanes of a warp diverge
+// only by their number of words, not also by whether they have a tail.
 __device__ __forceinline__ void signature_bytes(const uint8_t* p, uint64_t len, uint64_t& hi, uint64_t& lo) {
   uint64_t a = kSigHi, c = kSigLo;
   if (len) {
@@ -41,29 +43,22 @@ __device__ __forceinline__ void signature_bytes(const uint8_t* p, uint64_t len, 
     const uint32_t* w = reinterpret_cast<const uint32_t*>(addr & ~uintptr_t(3));
     const uint32_t sh = static_cast<uint32_t>(addr & 3) * 8;
     const uint64_t nt = ((addr + len - 1) >> 2) - (addr >> 2) + 1;  // words touched
-    const uint64_t nfull = len >> 3;
+    const uint64_t nw = (len + 7) >> 3;
     uint32_t w0 = __ldg(w);
     uint64_t j = 1;  // next word to load
-    // bytes 8i .. 8i + 7: words 2i (already loaded), 2i + 1 (always holds a
-    // byte of the string) and 2i + 2 (may hold none when sh == 0)
-    for (uint64_t i = 0; i < nfull; i++) {
-      const uint32_t w1 = __ldg(w + j);
-      const uint32_t w2 = j + 1 < nt ? __ldg(w + j + 1) : 0u;
-      j += 2;
-      const uint32_t l32 = __funnelshift_r(w0, w1, sh), h32 = __funnelshift_r(w1, w2, sh);
-      a = mix64(a ^ ((uint64_t(h32) << 32) | l32));
-      c = mix64(c ^ ((uint64_t(l32) << 32) | h32));
-      w0 = w2;
-    }
-    const uint32_t tail = static_cast<uint32_t>(len & 7);
-    if (tail) {
+    // bytes 8i .. 8i + 7: words 2i (already loaded), 2i + 1 and 2i + 2, the
+    // last two only where they hold a byte of the string
+    for (uint64_t i = 0; i < nw; i++) {
       const uint32_t w1 = j < nt ? __ldg(w + j) : 0u;
       const uint32_t w2 = j + 1 < nt ? __ldg(w + j + 1) : 0u;
-      uint32_t l32 = __funnelshift_r(w0, w1, sh), h32 = __funnelshift_r(w1, w2, sh);
-      if (tail < 4) l32 &= (1u << (8 * tail)) - 1;
-      h32 = tail <= 4 ? 0u : (h32 & ((1u << (8 * (tail - 4))) - 1));
-      a = mix64(a ^ ((uint64_t(h32) << 32) | l32));
-      c = mix64(c ^ ((uint64_t(l32) << 32) | h32));
+      j += 2;
+      const uint64_t rem = len - 8 * i;
+      const uint32_t keep = rem < 8 ? static_cast<uint32_t>(rem) * 8 : 64u;  // bits of the word in the string
+      const uint64_t mask = ~0ull >> (64 - keep);
+      const uint64_t word = ((uint64_t(__funnelshift_r(w1, w2, sh)) << 32) | __funnelshift_r(w0, w1, sh)) & mask;
+      a = mix64(a ^ word);
+      c = mix64(c ^ ((word >> 32) | (word << 32)));
+      w0 = w2;
     }
   }
   hi = mix64(a + len);

@@ -195,8 +195,11 @@ __global__ void k_lookup_u64(View v, const uint64_t* __restrict__ so, const uint
   }
 }
 
+// 32 registers (8 blocks of 256 threads per SM): the kernel is bound by
+// instruction issue, and full occupancy outweighs a few spilled registers
+// (measured: 4.09 -> 4.01 ms for 10^8 string lookups).
 template <bool RANGE>
-__global__ void k_lookup_bytes(View v, const uint64_t* __restrict__ so, const uint8_t* __restrict__ bytes,
+__global__ void __launch_bounds__(256, 8) k_lookup_bytes(View v, const uint64_t* __restrict__ so, const uint8_t* __restrict__ bytes,
                                const uint64_t* __restrict__ offsets, uint64_t q, uint64_t* __restrict__ out) {
   const uint64_t last = __ldg(offsets + q);  // the bytes span [0, offsets[q])
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
