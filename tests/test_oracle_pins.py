@@ -540,3 +540,23 @@ def test_inventory_overflow_entries_are_skipped(orc):
     for lst in (0, 1):
         for rank in list(range(700, 1100)) + list(range(16600, 17100)) + [nb]:
             assert orc.select_inventory(blob, lst, rank) == orc.select_linear(blob, lst, rank)
+
+
+def test_structured_lower_halves_behave_like_random_ones(orc):
+    # keys whose lower halves differ in a single bit: a family that is close
+    # to linear (one multiply round) maps such keys a fixed distance apart for
+    # every index and never finds a bijection; the first index must still
+    # follow Geometric(m!/m^m)
+    m, samples = 8, 400
+    p = math.factorial(m) / m ** m
+    rng = np.random.default_rng(77)
+    seeds = []
+    for _ in range(samples):
+        k = int(rng.integers(0, 1 << 62))
+        lo = (np.uint64(k) ^ (np.uint64(1) << np.arange(m, dtype=np.uint64))).astype(np.uint64)
+        s = orc.leaf_seed(lo, 0, cap=1 << 22)
+        assert s >= 0
+        seeds.append(s)
+    mean = float(np.mean(seeds)) + 1
+    sd = math.sqrt((1 - p) / p ** 2 / samples)
+    assert abs(mean - 1 / p) < 5 * sd, (mean, 1 / p)
