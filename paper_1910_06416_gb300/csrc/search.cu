@@ -95,10 +95,18 @@ struct SplitParams {
 // In mode 5 a field can overflow into the next one, so a match may be false,
 // but never missed: when every counted part has exactly unit keys no field
 // overflows.  A match is confirmed with the exact 64-bit count (mode 1).
+// 6: four parts of equal size (m = 4 unit < 256): the part is
+// floor(floor(h m / 2^32) / unit) = floor(4 h / 2^32), the top two bits of h,
+// counted in 8-bit fields with shifts only.
 template <int MODE>
 __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, const SplitParams& p,
                                             uint64_t kp) {
-  if (MODE == 3 || MODE == 4) {
+  if (MODE == 6) {
+    uint32_t acc = 0;
+#pragma unroll 4
+    for (uint32_t j = 0; j < p.m; j++) acc += 1u << ((family_top32(keys[j], kp) >> 27) & 0x18u);
+    return (acc & 0xFFFFFFu) == p.cum_target;
+  } else if (MODE == 3 || MODE == 4) {
     constexpr int F = MODE - 1;
     uint32_t acc = 0;
 #pragma unroll 4
@@ -198,6 +206,7 @@ __device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, 
     case 3: split_search_warp<3>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 4: split_search_warp<4>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 5: split_search_warp<5>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 6: split_search_warp<6>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     default: split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
   }
 }
@@ -249,78 +258,95 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
     group_sync(gid, gwarps);
     const uint32_t idx = task[gid];
     if (idx >= total) break;
-    const Node nd = a.split_in[idx];
-    const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
-    const uint64_t* table = a.table[cls];
-    const uint64_t w1 = table[kTableWords * nd.m + 1];
-    SplitParams sp;
-    sp.m = nd.m;
-    sp.unit = static_cast<uint32_t>(w1);
-    sp.fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
-    sp.bits = 32 - __clz(nd.m);
-    sp.magic = static_cast<uint32_t>((0x100000000ull + sp.unit - 1) / sp.unit);
-    const uint32_t fields = sp.fanout - 1;
-    sp.target = 0;
-    for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
-    sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
-    // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
-    int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
-    if (mode == 1) {
-      sp.nbits = 32 - __clz(sp.unit);
-      if (fields * sp.nbits <= 32) {
-        mode = 5;
-        sp.nmask = fields * sp.nbits == 32 ? ~0u : (1u << (fields * sp.nbits)) - 1;
-        sp.ntarget = 0;
-        for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * sp.nbits);
+    {
+      // search: the parameters live only for this scope, so the registers
+      // of the search loops are not shared with the partition step's state
+      const Node nd = a.split_in[idx];
+      const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
+      const uint64_t* table = a.table[cls];
+      const uint64_t w1 = table[kTableWords * nd.m + 1];
+      SplitParams sp;
+      sp.m = nd.m;
+      sp.unit = static_cast<uint32_t>(w1);
+      sp.fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
+      sp.bits = 32 - __clz(nd.m);
+      sp.magic = static_cast<uint32_t>((0x100000000ull + sp.unit - 1) / sp.unit);
+      const uint32_t fields = sp.fanout - 1;
+      sp.target = 0;
+      for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
+      sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
+      // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
+      int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+      if (sp.fanout == 4 && nd.m == 4 * sp.unit && nd.m < 256) {
+        mode = 6;
+        sp.cum_target = sp.unit | (sp.unit << 8) | (sp.unit << 16);
       }
-    }
-    if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= kMaxThresholdFanout && fields * sp.bits <= 32) {
-      mode = 1 + static_cast<int>(sp.fanout);
-      // T_k = ceil(k * unit * 2^32 / m); field k - 1 must count k * unit keys
-      sp.thr1 = static_cast<uint32_t>(((uint64_t(sp.unit) << 32) + nd.m - 1) / nd.m);
-      sp.thr2 = static_cast<uint32_t>(((uint64_t(2 * sp.unit) << 32) + nd.m - 1) / nd.m);
-      sp.cum_target = sp.unit + (fields >= 2 ? (2 * sp.unit) << sp.bits : 0u);
-      sp.inc1 = 1u << sp.bits;
-    }
-    const uint64_t stall = stall_threshold(table, nd.m);
-    const uint64_t limit = trial_limit(table, nd.m);
+      if (mode == 1) {
+        sp.nbits = 32 - __clz(sp.unit);
+        if (fields * sp.nbits <= 32) {
+          mode = 5;
+          sp.nmask = fields * sp.nbits == 32 ? ~0u : (1u << (fields * sp.nbits)) - 1;
+          sp.ntarget = 0;
+          for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * sp.nbits);
+        }
+      }
+      if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= kMaxThresholdFanout && fields * sp.bits <= 32) {
+        mode = 1 + static_cast<int>(sp.fanout);
+        // T_k = ceil(k * unit * 2^32 / m); field k - 1 must count k * unit keys
+        sp.thr1 = static_cast<uint32_t>(((uint64_t(sp.unit) << 32) + nd.m - 1) / nd.m);
+        sp.thr2 = static_cast<uint32_t>(((uint64_t(2 * sp.unit) << 32) + nd.m - 1) / nd.m);
+        sp.cum_target = sp.unit + (fields >= 2 ? (2 * sp.unit) << sp.bits : 0u);
+        sp.inc1 = 1u << sp.bits;
+      }
+      const uint64_t stall = stall_threshold(table, nd.m);
+      const uint64_t limit = trial_limit(table, nd.m);
 
-    const uint64_t* src = a.keys[depth & 1] + nd.start;
-    uint64_t* dst = a.keys[(depth + 1) & 1] + nd.start;
-    const bool in_smem = nd.m <= cap;
-    if (in_smem)
-      for (uint32_t j = tig; j < nd.m; j += gthreads) mine[j] = src[j];
-    if (leader) best[gid] = ~0ull;
-    if (tig < 16) fill[gid][tig] = 0;
-    group_sync(gid, gwarps);
+      const uint64_t* src = a.keys[depth & 1] + nd.start;
+      const bool in_smem = nd.m <= cap;
+      if (in_smem)
+        for (uint32_t j = tig; j < nd.m; j += gthreads) mine[j] = src[j];
+      if (leader) best[gid] = ~0ull;
+      if (tig < 16) fill[gid][tig] = 0;
+      group_sync(gid, gwarps);
 
-    if (in_smem)
-      split_search(mine, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
-    else
-      split_search(src, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
-    group_sync(gid, gwarps);
+      if (in_smem)
+        split_search(mine, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+      else
+        split_search(src, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+      group_sync(gid, gwarps);
+    }
 
     const uint64_t seed = best[gid];
     if (!*reinterpret_cast<volatile int*>(a.error)) {
+      // the node again: partition its keys with the index found
+      const Node nd = a.split_in[idx];
+      const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
+      const uint64_t* table = a.table[cls];
+      const uint64_t w1 = table[kTableWords * nd.m + 1];
+      const uint32_t unit = static_cast<uint32_t>(w1), fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
+      const bool divide = nd.m >= 65536 || unit < 2;
+      const uint32_t magic = divide ? 0u : static_cast<uint32_t>((0x100000000ull + unit - 1) / unit);
+      const uint64_t* src = a.keys[depth & 1] + nd.start;
+      uint64_t* dst = a.keys[(depth + 1) & 1] + nd.start;
       if (leader) {
         a.seeds[nd.slot] = seed;
         a.sizes[nd.slot] = nd.m;
       }
       // partition the keys into the children's ranges of the other array
       const uint64_t kp = family_key(seed, depth);
-      const uint64_t* from = in_smem ? mine : src;
+      const uint64_t* from = nd.m <= cap ? mine : src;
       for (uint32_t j = tig; j < nd.m; j += gthreads) {
         const uint64_t x = from[j];
         const uint32_t v = phi_pre(x, kp, nd.m);
-        const uint32_t part = min(mode == 2 ? v / sp.unit : __umulhi(v, sp.magic), sp.fanout - 1);
+        const uint32_t part = min(divide ? v / unit : __umulhi(v, magic), fanout - 1);
         const uint32_t pos = atomicAdd(&fill[gid][part], 1u);
-        const uint32_t at = part * sp.unit + pos;
+        const uint32_t at = part * unit + pos;
         if (at < nd.m)
           dst[at] = x;
         else
           set_error(a.error, RECSPLIT_E_INVALID);  // unreachable for a correct split
       }
-      if (wig == 0) emit_children(a, nd, table, a.leaf_of[cls], sp.unit, sp.fanout, lane);
+      if (wig == 0) emit_children(a, nd, table, a.leaf_of[cls], unit, fanout, lane);
     }
     group_sync(gid, gwarps);
   }
