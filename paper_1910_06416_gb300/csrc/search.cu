@@ -86,7 +86,8 @@ struct SplitParams {
   uint32_t thr1, thr2;      // T_1, T_2 (threshold modes)
   uint32_t inc1;            // 1 << B
   uint32_t cum_target;      // sum over k of k * unit << ((k - 1) * B)
-  uint32_t nbits, nmask, ntarget;  // narrow fields (mode 5): 2^nbits > unit
+  uint32_t nbits, nmask, ntarget;  // narrow fields (modes 5, 7): 2^nbits > unit
+  bool confirm;                    // mode 7: fields can overflow, confirm matches exactly
 };
 
 // MODE 0: 32-bit fields + magic; 1: 64-bit fields + magic; 2: 64-bit +
@@ -98,6 +99,9 @@ struct SplitParams {
 // 6: four parts of equal size (m = 4 unit < 256): the part is
 // floor(floor(h m / 2^32) / unit) = floor(4 h / 2^32), the top two bits of h,
 // counted in 8-bit fields with shifts only.
+// 7: F parts of equal size (m = F unit): the part is floor(F h / 2^32), one
+// multiply-high instead of two, counted in nbits-bit fields; when a field
+// can overflow (2^nbits <= m) a match is confirmed exactly as in mode 5.
 template <int MODE>
 __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, const SplitParams& p,
                                             uint64_t kp) {
@@ -106,6 +110,11 @@ __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, c
 #pragma unroll 4
     for (uint32_t j = 0; j < p.m; j++) acc += 1u << ((family_top32(keys[j], kp) >> 27) & 0x18u);
     return (acc & 0xFFFFFFu) == p.cum_target;
+  } else if (MODE == 7) {
+    uint32_t acc = 0;
+#pragma unroll 4
+    for (uint32_t j = 0; j < p.m; j++) acc += shl32(1u, __umulhi(family_top32(keys[j], kp), p.fanout) * p.nbits);
+    return (acc & p.nmask) == p.ntarget;
   } else if (MODE == 3 || MODE == 4) {
     constexpr int F = MODE - 1;
     uint32_t acc = 0;
@@ -188,7 +197,7 @@ __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ k
     }
     const uint64_t kp = family_key(base + lane, depth);
     bool ok = split_trial<MODE>(keys, sp, kp);
-    if (MODE == 5 && ok) ok = split_trial<1>(keys, sp, kp);
+    if ((MODE == 5 || (MODE == 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
     const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
     if (hits) {
       if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(best), base + __ffs(hits) - 1);
@@ -207,6 +216,7 @@ __device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, 
     case 4: split_search_warp<4>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 5: split_search_warp<5>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     case 6: split_search_warp<6>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 7: split_search_warp<7>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
     default: split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
   }
 }
@@ -280,8 +290,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
       if (sp.fanout == 4 && nd.m == 4 * sp.unit && nd.m < 256) {
         mode = 6;
         sp.cum_target = sp.unit | (sp.unit << 8) | (sp.unit << 16);
+      } else if (sp.fanout >= 5 && nd.m == sp.fanout * sp.unit && sp.unit >= 2 && nd.m < 65536) {
+        const uint32_t nb = nd.m < 256 && fields * 8 <= 32 ? 8 : 32 - __clz(sp.unit);
+        if (fields * nb <= 32) {
+          mode = 7;
+          sp.confirm = (1u << nb) <= nd.m;
+          sp.nbits = nb;
+          sp.nmask = fields * nb == 32 ? ~0u : (1u << (fields * nb)) - 1;
+          sp.ntarget = 0;
+          for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * nb);
+        }
       }
-      if (mode == 1) {
+      if (mode == 1 && sp.fanout * sp.unit != nd.m) {
         sp.nbits = 32 - __clz(sp.unit);
         if (fields * sp.nbits <= 32) {
           mode = 5;
