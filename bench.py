@@ -174,7 +174,7 @@ def traffic_from_profiles(kernel_tag, source="search.cu", key="dram_bytes_per_la
         return None
 
 
-def timed_repeats(fn, min_s=10.0, max_reps=50):
+def timed_repeats(fn, min_s=10.0, max_reps=100000):
     """Runs fn until at least min_s seconds have passed (at most max_reps
     times); returns (repetitions, seconds)."""
     reps, t0 = 0, time.perf_counter()

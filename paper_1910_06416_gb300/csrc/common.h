@@ -183,8 +183,9 @@ struct BuildOptions {
 int build_sets(const SetInput* sets, uint32_t count, const BuildOptions& opt, cudaStream_t s, Handle** out);
 // allow_scratch = false: allocate nothing (no per-batch decode of the lists)
 int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s, bool allow_scratch = true);
+// any_range: some view has a leaf range extra (perfect, non-minimal variant)
 int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
-                cudaStream_t s);
+                cudaStream_t s, bool any_range = true);
 // Batched lookups over several structures with at least as many queries as
 // the structures have buckets: s_i, o_i of every bucket of every structure
 // are decoded into one pooled array *so (the caller frees it, stream-ordered,

@@ -230,14 +230,16 @@ __global__ void k_ef_decode_views(const View* __restrict__ views, const uint64_t
   }
 }
 
+// ANY_RANGE: some structure of the batch has a leaf range extra.
+template <bool ANY_RANGE>
 __global__ void k_lookup_many(const View* __restrict__ views, const uint32_t* __restrict__ ids,
                               const uint64_t* __restrict__ keys, uint64_t q, uint64_t* __restrict__ out) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t hi, lo;
     signature_u64(__ldg(keys + i), hi, lo);
     const View& v = views[__ldg(ids + i)];
-    out[i] = v.extra ? (v.so ? lookup_decoded<true>(v, v.so, hi, lo) : lookup_one<true>(v, hi, lo))
-                     : (v.so ? lookup_decoded<false>(v, v.so, hi, lo) : lookup_one<false>(v, hi, lo));
+    out[i] = ANY_RANGE && v.extra ? (v.so ? lookup_decoded<true>(v, v.so, hi, lo) : lookup_one<true>(v, hi, lo))
+                                  : (v.so ? lookup_decoded<false>(v, v.so, hi, lo) : lookup_one<false>(v, hi, lo));
   }
 }
 
@@ -281,7 +283,7 @@ int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t*
 }
 
 int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
-                cudaStream_t s) {
+                cudaStream_t s, bool any_range) {
   if (q == 0) return RECSPLIT_OK;
   LookupRange range;
   int dev = 0, sms = 0;
@@ -290,7 +292,7 @@ int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_ke
   const int block = 256;
   const uint64_t want = (q + block - 1) / block;
   const unsigned grid = static_cast<unsigned>(want < uint64_t(sms) * 64 ? want : uint64_t(sms) * 64);
-  k_lookup_many<<<grid, block, 0, s>>>(d_views, d_ids, d_keys, q, d_out);
+  (any_range ? k_lookup_many<true> : k_lookup_many<false>)<<<grid, block, 0, s>>>(d_views, d_ids, d_keys, q, d_out);
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;
