@@ -147,6 +147,9 @@ def test_serialize_round_trip(rs, orc):
     # a structure serialized by the oracle loads and answers the same
     s3 = rs.Structure.deserialize(orc.build_u64(keys, 5, 5))
     assert np.array_equal(gpu_lookup_u64(s3, keys), gpu_lookup_u64(s, keys))
+    # the output range read back from the lists is n for a minimal structure
+    assert s.stats()["range_size"] == s2.stats()["range_size"] == s3.stats()["range_size"] == keys.shape[0]
+    assert s3.stats()["leaf_extra"] == 0
 
 
 def test_repeated_keys_are_reported(rs):
