@@ -134,17 +134,34 @@ bool on_device(const void* p) {
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
-// Device address of page-locked host memory (cudaHostAlloc, cudaHostRegister,
-// a pinned torch tensor), or null for other memory.  The GPU reads such
-// memory directly over the host link, so a build that reads its keys once
-// takes them from there instead of staging a copy first.
+// Whether kernels of the current device can read ordinary (pageable) host
+// memory through the host's page tables (a coherent CPU-GPU link, as on
+// Grace-based systems).
+bool pageable_readable() {
+  int dev = 0, access = 0, host_tables = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&access, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return access && host_tables;
+}
+
+// Device address under which a kernel reads host memory in place: for
+// page-locked memory (cudaHostAlloc, cudaHostRegister, a pinned torch tensor)
+// its device alias, for pageable memory the pointer itself where the device
+// reads pageable memory through the host's page tables; else null.  A build
+// reads its keys once, so it takes them from there instead of staging a copy.
 void* pinned_device_alias(const void* p) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
+  if (attr.type == cudaMemoryTypeHost) return attr.devicePointer;
+  if (attr.type == cudaMemoryTypeUnregistered && pageable_readable()) return const_cast<void*>(p);
+  return nullptr;
 }
 
 // Device copy of a host buffer (or the device pointer itself).
