@@ -190,8 +190,10 @@ typedef struct recsplit_profile {
   uint32_t split_levels;  /* launches of the split search (one per tree level)  */
 } recsplit_profile_t;
 
-/* Turns per-build profiling on (non-zero) or off (0) for the calling host
- * thread.  Profiling adds events and one reduction kernel per build. */
+/* Per-build profiling for the calling host thread: 0 off; 1 phase events
+ * and the algorithmic work counts (two small kernels after the build's last
+ * phase); 2 phase events only (the work fields of the profile are 0).  Other
+ * values fail with RECSPLIT_E_INVALID. */
 int recsplit_set_profiling(int enabled);
 
 /* Profile of the last successful build on the calling host thread. */

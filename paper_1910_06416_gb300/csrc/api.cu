@@ -109,12 +109,14 @@ int wait_stream(cudaStream_t s, int* d_error, uint32_t ms, double start_ms) {
   return cancelled ? fail(RECSPLIT_E_TIMEOUT, "build cancelled after its time limit") : RECSPLIT_OK;
 }
 
-static thread_local bool g_profiling = false;
+static thread_local int g_profiling = 0;  // 0 off, 1 events and work counts, 2 events only
 static thread_local recsplit_profile_t g_profile = {};
 static thread_local bool g_have_profile = false;
 static thread_local uint64_t g_launches = 0;
 
-bool profiling_enabled() { return g_profiling; }
+bool profiling_enabled() { return g_profiling != 0; }
+bool work_counting_enabled() { return g_profiling == 1; }
+int profiling_mode() { return g_profiling; }
 void store_profile(const recsplit_profile_t& p) {
   g_profile = p;
   g_have_profile = true;
@@ -551,7 +553,8 @@ const char* recsplit_strerror(int code) {
 const char* recsplit_last_error(void) { return g_last_error.c_str(); }
 
 int recsplit_set_profiling(int enabled) {
-  g_profiling = enabled != 0;
+  if (enabled < 0 || enabled > 2) return fail(RECSPLIT_E_INVALID, "profiling mode must be 0, 1 or 2");
+  g_profiling = enabled;
   return RECSPLIT_OK;
 }
 

@@ -900,7 +900,8 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   count_launch();
   timer.mark();
   unsigned long long* work = nullptr;
-  if (timer.on) {
+  const bool count_work = timer.on && work_counting_enabled();
+  if (count_work) {
     uint32_t* code_leaf;
     if ((rc = sc.alloc(&work, 6)) || (rc = sc.alloc(&code_leaf, K + 1))) return rc;
     RS_CUDA(cudaMemsetAsync(work, 0, 6 * sizeof(unsigned long long), s));
@@ -913,7 +914,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   }
   RS_CUDA(cudaGetLastError());
   unsigned long long w[6] = {0, 0, 0, 0, 0, 0};
-  if (timer.on) RS_CUDA(cudaMemcpyAsync(w, work, sizeof(w), cudaMemcpyDeviceToHost, s));
+  if (count_work) RS_CUDA(cudaMemcpyAsync(w, work, sizeof(w), cudaMemcpyDeviceToHost, s));
   RS_CUDA(cudaStreamSynchronize(s));
 
   for (uint32_t i = 0; i < count; i++) {

@@ -135,7 +135,9 @@ uint32_t timeout_ms();
 double steady_ms();
 
 // ---------------------------------------------------------------- tracing
-bool profiling_enabled();
+bool profiling_enabled();       // phase events on
+bool work_counting_enabled();   // and the work-count kernels
+int profiling_mode();
 void store_profile(const recsplit_profile_t& p);
 void count_launch(uint32_t k = 1);
 uint32_t launches_since(uint64_t mark);

@@ -87,8 +87,8 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
   in.leaf = leaf_size;
   in.bucket_size = bucket_size;
 
-  const bool was_profiling = profiling_enabled();
-  recsplit_set_profiling(1);
+  const int was_profiling = profiling_mode();
+  recsplit_set_profiling(2);  // phase events only
   const recsplit_tuning_t start = tuning_for(leaf_size);
   recsplit_tuning_t best = start;
   double leaf_ms = 0, split_ms = 0;
@@ -153,7 +153,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
       }
     }
   } while (false);
-  recsplit_set_profiling(was_profiling ? 1 : 0);
+  recsplit_set_profiling(was_profiling);
   cudaFreeAsync(keys, s);
   set_tuning_for(leaf_size, rc ? start : best);
   if (rc) return rc;

@@ -417,8 +417,9 @@ def recsplit_golomb_rice_params_extra(leaf_size: int, leaf_extra: int, m_hi: int
     return out
 
 
-def recsplit_set_profiling(enabled: bool) -> None:
-    _check(lib().recsplit_set_profiling(1 if enabled else 0), "recsplit_set_profiling")
+def recsplit_set_profiling(enabled) -> None:
+    """False/0: off; True/1: phase events and work counts; 2: phase events only."""
+    _check(lib().recsplit_set_profiling(int(enabled)), "recsplit_set_profiling")
 
 
 def recsplit_last_profile() -> dict:

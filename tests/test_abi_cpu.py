@@ -79,6 +79,15 @@ def test_perfect_build_arguments_rejected_before_device_work(rs):
     assert e.value.code == rs.E_INVALID
 
 
+def test_profiling_modes(rs):
+    for mode in (0, 1, 2, True, False):
+        rs.recsplit_set_profiling(mode)
+    for bad in (-1, 3):
+        with pytest.raises(rs.RecSplitError):
+            rs.recsplit_set_profiling(bad)
+    rs.recsplit_set_profiling(0)
+
+
 def test_tuning_shapes_are_validated(rs):
     t = rs.recsplit_get_tuning(8)
     assert t["leaf_warps"] in (1, 2, 4, 8)

@@ -46,3 +46,19 @@ def test_bits_per_key_independent_of_n(rs):
         out.append(rs.recsplit_stats(h)["bits_per_key"])
         rs.recsplit_free(h)
     assert max(out) - min(out) < 0.03, out
+
+
+def test_profiling_events_only_and_deterministic_work(rs):
+    keys = torch.from_numpy(inputs.u64_keys(200_000, 5).view(np.int64)).cuda()
+    rs.recsplit_set_profiling(2)  # phase events, no work-count kernels
+    rs.recsplit_free(rs.recsplit_build_u64(keys, 8, 100))
+    p = rs.recsplit_last_profile()
+    assert p["ms_total"] > 0 and p["leaf_evals"] == 0 and p["split_evals"] == 0
+    rs.recsplit_set_profiling(1)
+    counts = []
+    for _ in range(2):
+        rs.recsplit_free(rs.recsplit_build_u64(keys, 8, 100))
+        p = rs.recsplit_last_profile()
+        counts.append((p["leaf_evals"], p["split_evals"], p["leaf_trials"], p["split_trials"]))
+    rs.recsplit_set_profiling(0)
+    assert counts[0] == counts[1] and counts[0][0] > 0  # the searches are deterministic
