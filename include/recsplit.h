@@ -107,7 +107,9 @@ int recsplit_build(const uint64_t* keys, uint64_t n, uint32_t leaf_size, uint32_
 
 /* One key set of a batched build: 64-bit keys (keys != NULL) or byte strings
  * (bytes and offsets with n + 1 entries), in device memory, with its own
- * leaf size and bucket size. */
+ * leaf size and bucket size, and leaf range extra (0 for the minimal perfect
+ * hash function; > 0 for the non-minimal variant of
+ * recsplit_build_perfect_u64). */
 typedef struct recsplit_keyset {
   const uint64_t* keys;
   const uint8_t* bytes;
@@ -115,6 +117,8 @@ typedef struct recsplit_keyset {
   uint64_t n;
   uint32_t leaf_size;
   uint32_t bucket_size;
+  uint32_t leaf_extra;
+  uint32_t reserved;  /* 0 */
 } recsplit_keyset_t;
 
 /* Builds count independent structures in one pass (Sec. 4 applied to every

@@ -308,6 +308,7 @@ int recsplit_build_batch(const recsplit_keyset_t* sets, uint32_t count, void* st
     recsplit_t* dummy = nullptr;
     int rc = check_build_args(k.n, k.leaf_size, k.bucket_size, &dummy);
     if (rc) return rc;
+    if (k.leaf_extra > 32 - k.leaf_size) return fail(RECSPLIT_E_INVALID, "leaf_size + leaf_extra must be at most 32");
     if (k.n) {
       const bool u64 = k.keys != nullptr;
       if (u64 ? !on_device(k.keys) : (!k.bytes || !k.offsets || !on_device(k.bytes) || !on_device(k.offsets)))
@@ -319,6 +320,7 @@ int recsplit_build_batch(const recsplit_keyset_t* sets, uint32_t count, void* st
     in[i].keys.n = k.n;
     in[i].leaf = k.leaf_size;
     in[i].bucket_size = k.bucket_size;
+    in[i].leaf_extra = k.leaf_extra;
   }
   std::vector<Handle*> hs(count, nullptr);
   BuildOptions opt;

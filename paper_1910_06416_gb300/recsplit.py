@@ -44,7 +44,8 @@ class Profile(C.Structure):
 
 class KeySet(C.Structure):
     _fields_ = [("keys", C.c_void_p), ("bytes", C.c_void_p), ("offsets", C.c_void_p), ("n", C.c_uint64),
-                ("leaf_size", C.c_uint32), ("bucket_size", C.c_uint32)]
+                ("leaf_size", C.c_uint32), ("bucket_size", C.c_uint32), ("leaf_extra", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class ServerConfig(C.Structure):
@@ -232,15 +233,21 @@ def recsplit_lookup_u64(h: int, keys, out, stream=None) -> None:
 def recsplit_build_batch(sets, stream=None) -> list[int]:
     """Build one structure per set in one pass.  `sets`: sequence of
     (keys, leaf_size, bucket_size) for 64-bit keys or
-    (bytes, offsets, leaf_size, bucket_size) for byte strings (device arrays)."""
+    (bytes, offsets, leaf_size, bucket_size) for byte strings (device arrays);
+    a dict {"leaf_extra": e} as the last element builds that set as the
+    perfect, non-minimal variant."""
     arr = (KeySet * max(1, len(sets)))()
     for i, st in enumerate(sets):
+        extra = 0
+        if st and isinstance(st[-1], dict):
+            extra = int(st[-1].get("leaf_extra", 0))
+            st = st[:-1]
         if len(st) == 3:
             keys, leaf, b = st
-            arr[i] = KeySet(_ptr(keys), None, None, _count(keys), leaf, b)
+            arr[i] = KeySet(_ptr(keys), None, None, _count(keys), leaf, b, extra, 0)
         else:
             data, offs, leaf, b = st
-            arr[i] = KeySet(None, _ptr(data), _ptr(offs), _count(offs) - 1, leaf, b)
+            arr[i] = KeySet(None, _ptr(data), _ptr(offs), _count(offs) - 1, leaf, b, extra, 0)
     outs = (C.c_void_p * max(1, len(sets)))()
     _check(lib().recsplit_build_batch(C.cast(arr, C.c_void_p), len(sets), _stream(stream), C.cast(outs, C.c_void_p)),
            "recsplit_build_batch")

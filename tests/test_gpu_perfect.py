@@ -124,3 +124,18 @@ def test_perfect_full_size_leaf8_bucket100(rs, orc):
     assert torch.unique(out).numel() == n and int(out.max()) < r
     sample = np.random.default_rng(5).integers(0, n, 20000)
     assert np.array_equal(host_u64(out)[sample], orc.lookup_u64(ref, keys[sample]))
+
+
+def test_batched_build_mixes_minimal_and_perfect_sets(rs, orc):
+    plan = [(20000, 8, 100, 0), (15000, 8, 100, 2), (30000, 5, 5, 1), (8000, 12, 9, 4), (5000, 8, 100, 0),
+            (1, 8, 100, 3), (0, 5, 5, 2)]
+    keys = [inputs.u64_keys(n, 80 + i) for i, (n, _, _, _) in enumerate(plan)]
+    sets = [(dev_u64(k), l, b, {"leaf_extra": e}) for k, (n, l, b, e) in zip(keys, plan)]
+    hs = rs.recsplit_build_batch(sets)
+    try:
+        for h, k, (n, l, b, e) in zip(hs, keys, plan):
+            assert np.array_equal(rs.recsplit_serialize(h), orc.build_u64(k, l, b, threads=4, extra=e)), (n, l, b, e)
+            assert rs.recsplit_stats(h)["leaf_extra"] == e
+    finally:
+        for h in hs:
+            rs.recsplit_free(h)
