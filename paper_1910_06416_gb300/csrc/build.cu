@@ -192,12 +192,19 @@ __global__ void k_roots(const uint64_t* __restrict__ counts, const uint64_t* __r
     const DevSet& st = sets[bset[b]];
     Node nd{static_cast<uint32_t>(bstart[b]), static_cast<uint32_t>(m), static_cast<uint32_t>(cbase[b]),
             st.cls << 8};
+    Node* q;
+    uint32_t *cnt, cap;
     if (m > st.leaf)
-      a.split_in[atomicAdd(a.split_in_count, 1u)] = nd;
+      q = a.split_in, cnt = a.split_in_count, cap = a.split_cap;
     else if (m == st.leaf)
-      a.full_q[st.cls][atomicAdd(a.full_n + st.cls, 1u)] = nd;
+      q = a.full_q[st.cls], cnt = a.full_n + st.cls, cap = a.full_cap[st.cls];
     else
-      a.part_q[st.cls][atomicAdd(a.part_n + st.cls, 1u)] = nd;
+      q = a.part_q[st.cls], cnt = a.part_n + st.cls, cap = a.part_cap[st.cls];
+    const uint32_t at = atomicAdd(cnt, 1u);
+    if (at < cap)
+      q[at] = nd;
+    else
+      atomicCAS(a.error, 0, RECSPLIT_E_INVALID);
   }
 }
 
@@ -692,11 +699,14 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
       a.leaf_of[c] = class_leaf[c];
       a.extra_of[c] = class_extra[c];
       a.full_q[c] = q;
+      a.full_cap[c] = static_cast<uint32_t>(full_cap[c]);
       q += full_cap[c];
       a.part_q[c] = q;
+      a.part_cap[c] = static_cast<uint32_t>(part_cap[c]);
       q += part_cap[c];
     }
   }
+  a.split_cap = static_cast<uint32_t>(split_cap);
   a.work_counter = counters + 2;
   a.full_n = counters + 3;
   a.part_n = counters + 3 + kMaxClasses;

@@ -227,6 +227,9 @@ struct SearchArgs {
   int* error;                             // first error code
   uint32_t cls;                           // class of a leaf launch
   uint32_t extra_of[kMaxClasses];         // leaf range extra per class
+  // queue capacities: an append beyond one sets RECSPLIT_E_INVALID in *error
+  // instead of writing (the sizes are computed to suffice; this guards them)
+  uint32_t split_cap, full_cap[kMaxClasses], part_cap[kMaxClasses];
 };
 
 int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s);

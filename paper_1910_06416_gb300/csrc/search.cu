@@ -244,10 +244,17 @@ __device__ void emit_children(const SearchArgs& a, const Node& nd, const uint64_
     const uint32_t leader = __ffs(ballot) - 1;
     Node* q = c == 0 ? a.full_q[c_of_node] : (c == 1 ? a.part_q[c_of_node] : a.split_out);
     uint32_t* cnt = c == 0 ? a.full_n + c_of_node : (c == 1 ? a.part_n + c_of_node : a.split_out_count);
+    const uint32_t cap = c == 0 ? a.full_cap[c_of_node] : (c == 1 ? a.part_cap[c_of_node] : a.split_cap);
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(cnt, __popc(ballot));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (mine) q[base + __popc(ballot & ((1u << lane) - 1))] = child;
+    const uint32_t at = base + __popc(ballot & ((1u << lane) - 1));
+    if (mine) {
+      if (at < cap)
+        q[at] = child;
+      else
+        set_error(a.error, RECSPLIT_E_INVALID);  // a queue would overflow: never for correct sizes
+    }
   }
 }
 
