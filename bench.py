@@ -195,9 +195,16 @@ def cpu_baseline(a, keys_np):
     ns = min(a.n, 10_000_000)
     sub = inputs.ByteKeys(keys_np.data[:int(keys_np.offsets[ns])], keys_np.offsets[:ns + 1])
     reps, dt = timed_repeats(lambda: oracle.build_bytes(sub.data, sub.offsets, a.leaf, a.bucket, threads=threads))
+    # and on one core, on the first 10^6 keys
+    n1 = min(a.n, 1_000_000)
+    s1 = inputs.ByteKeys(keys_np.data[:int(keys_np.offsets[n1])], keys_np.offsets[:n1 + 1])
+    reps1, dt1 = timed_repeats(lambda: oracle.build_bytes(s1.data, s1.offsets, a.leaf, a.bucket, threads=1),
+                               min_s=5.0)
     return {"value": ns * reps / dt, "unit": "keys/s", "cores": threads, "kind": "oracle",
             "sample": f"oracle builds of the first {ns} keys of the workload (same l, b; {threads} threads), "
-                      f"{reps} builds in {dt:.1f} s"}
+                      f"{reps} builds in {dt:.1f} s",
+            "single_core": {"value": n1 * reps1 / dt1, "unit": "keys/s", "cores": 1,
+                            "sample": f"{reps1} builds of the first {n1} keys on one thread in {dt1:.1f} s"}}
 
 
 def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5):
