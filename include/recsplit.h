@@ -14,7 +14,10 @@
  * Conventions for every call:
  *  - Pointers to keys, queries and outputs may point to host memory or to
  *    device memory of the current CUDA device; the library detects which and
- *    copies host buffers itself (inside the call, on `stream`).
+ *    handles host buffers itself (inside the call, on `stream`): builds read
+ *    host keys in place where the device can (page-locked memory, or pageable
+ *    memory on systems whose GPU reads the host's page tables) and stage
+ *    them otherwise.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Build
  *    returns once the structure is complete on the device; lookups with
  *    device outputs return as soon as the work is queued on `stream`, lookups
@@ -38,7 +41,9 @@ extern "C" {
 
 #define RECSPLIT_OK 0
 #define RECSPLIT_E_INVALID (-1)      /* bad argument: leaf_size outside [1,24], bucket_size outside
-                                        [1,65535], n >= 2^32, NULL pointer, bad serialized data */
+                                        [1,65535], n >= 2^32, NULL pointer, bad serialized data,
+                                        decreasing byte-string offsets; or an internal check
+                                        (queue capacity) that failed */
 #define RECSPLIT_E_DUPLICATE (-2)    /* two keys share their 64-bit lower signature half (for
                                         64-bit keys: the key set has a repeated key) */
 #define RECSPLIT_E_SEARCH_LIMIT (-4) /* a split or bijection search passed 2^36 trials */
