@@ -183,24 +183,44 @@ __global__ void k_scatter(const uint32_t* __restrict__ bucket, const uint64_t* _
   }
 }
 
+// Every bucket of two or more keys is appended to the queue of its kind
+// (split node, full leaf, partial leaf).  The lanes of a warp that append to
+// the same queue take their slots with one atomic: with buckets of a few keys
+// there are millions of appends to a handful of counters, and one atomic per
+// bucket on the same address serialises them.
 __global__ void k_roots(const uint64_t* __restrict__ counts, const uint64_t* __restrict__ bstart,
                         const uint64_t* __restrict__ cbase, const uint32_t* __restrict__ bset,
                         const DevSet* __restrict__ sets, uint64_t nbt, SearchArgs a) {
-  for (uint64_t b = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; b < nbt; b += uint64_t(gridDim.x) * blockDim.x) {
-    const uint64_t m = counts[b];
-    if (m < 2) continue;
-    const DevSet& st = sets[bset[b]];
-    Node nd{static_cast<uint32_t>(bstart[b]), static_cast<uint32_t>(m), static_cast<uint32_t>(cbase[b]),
-            st.cls << 8};
-    Node* q;
-    uint32_t *cnt, cap;
-    if (m > st.leaf)
-      q = a.split_in, cnt = a.split_in_count, cap = a.split_cap;
-    else if (m == st.leaf)
-      q = a.full_q[st.cls], cnt = a.full_n + st.cls, cap = a.full_cap[st.cls];
-    else
-      q = a.part_q[st.cls], cnt = a.part_n + st.cls, cap = a.part_cap[st.cls];
-    const uint32_t at = atomicAdd(cnt, 1u);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  // the loop bound is uniform across the warp: every lane reaches the ballot
+  for (uint64_t w0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); w0 < nbt; w0 += stride) {
+    const uint64_t b = w0 + lane;
+    const uint64_t m = b < nbt ? counts[b] : 0;
+    const bool want = m >= 2;
+    Node nd{};
+    Node* q = nullptr;
+    uint32_t* cnt = nullptr;
+    uint32_t cap = 0;
+    if (want) {
+      const DevSet& st = sets[bset[b]];
+      nd = Node{static_cast<uint32_t>(bstart[b]), static_cast<uint32_t>(m), static_cast<uint32_t>(cbase[b]),
+                st.cls << 8};
+      if (m > st.leaf)
+        q = a.split_in, cnt = a.split_in_count, cap = a.split_cap;
+      else if (m == st.leaf)
+        q = a.full_q[st.cls], cnt = a.full_n + st.cls, cap = a.full_cap[st.cls];
+      else
+        q = a.part_q[st.cls], cnt = a.part_n + st.cls, cap = a.part_cap[st.cls];
+    }
+    const uint32_t active = __ballot_sync(0xFFFFFFFFu, want);
+    if (!want) continue;
+    const uint32_t peers = __match_any_sync(active, reinterpret_cast<unsigned long long>(cnt));
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(cnt, static_cast<uint32_t>(__popc(peers)));
+    base = __shfl_sync(peers, base, leader);
+    const uint32_t at = base + __popc(peers & ((1u << lane) - 1));
     if (at < cap)
       q[at] = nd;
     else
