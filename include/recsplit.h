@@ -42,8 +42,9 @@ extern "C" {
 #define RECSPLIT_OK 0
 #define RECSPLIT_E_INVALID (-1)      /* bad argument: leaf_size outside [1,24], bucket_size outside
                                         [1,65535], n >= 2^32, NULL pointer, bad serialized data,
-                                        decreasing byte-string offsets; or an internal check
-                                        (queue capacity) that failed */
+                                        decreasing byte-string offsets, a bucket whose code
+                                        reaches 2^32 bits (over 10^9 keys in one bucket); or an
+                                        internal check (queue capacity) that failed */
 #define RECSPLIT_E_DUPLICATE (-2)    /* two keys share their 64-bit lower signature half (for
                                         64-bit keys: the key set has a repeated key) */
 #define RECSPLIT_E_SEARCH_LIMIT (-4) /* a split or bijection search passed 2^36 trials */

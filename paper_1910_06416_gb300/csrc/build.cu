@@ -232,10 +232,13 @@ __global__ void k_roots(const uint64_t* __restrict__ counts, const uint64_t* __r
 // Bits of bucket b: fixed bits of its tree (table) + unary parts (i >> r) + 1.
 // After a failed search (error set) the slots of unsearched nodes were never
 // written: the lengths are then not computed (the build reports the error).
+// Lookups address the bits of a bucket with 32-bit offsets, so a bucket whose
+// code reaches 2^32 bits (more than a billion keys in one bucket) fails the
+// build with RECSPLIT_E_INVALID.
 __global__ void k_bucket_bits(const uint64_t* __restrict__ counts, const uint64_t* __restrict__ cbase,
                               const uint64_t* __restrict__ seeds, const uint32_t* __restrict__ sizes,
                               const uint32_t* __restrict__ bset, const DevSet* __restrict__ sets, ClassTables ct,
-                              uint64_t nbt, const int* __restrict__ error, uint64_t* __restrict__ bits) {
+                              uint64_t nbt, int* __restrict__ error, uint64_t* __restrict__ bits) {
   const bool failed = *reinterpret_cast<const volatile int*>(error) != 0;
   for (uint64_t b = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; b < nbt; b += uint64_t(gridDim.x) * blockDim.x) {
     const uint32_t cls = sets[bset[b]].cls;
@@ -248,6 +251,7 @@ __global__ void k_bucket_bits(const uint64_t* __restrict__ counts, const uint64_
         const uint32_t r = sz <= ct.mmax[cls] ? static_cast<uint32_t>(table[kTableWords * sz + 1] >> 40) & 31 : 0;
         len += (seeds[c] >> r) + 1;
       }
+      if (len >= (1ull << 32)) atomicCAS(error, 0, RECSPLIT_E_INVALID);
     }
     bits[b] = len;
   }
@@ -850,7 +854,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   RS_CUDA(cudaStreamSynchronize(s));
   if (herr == RECSPLIT_E_DUPLICATE) return fail(herr, "two keys share their lower signature half (duplicate keys)");
   if (herr == RECSPLIT_E_SEARCH_LIMIT) return fail(herr, "seed search exceeded its limit");
-  if (herr) return fail(herr, "internal consistency check failed during the search");
+  if (herr) return fail(herr, "a queue capacity or bucket code length check failed");
 
   // headers and layouts; one arena for all structures (256-byte aligned each)
   std::vector<uint64_t> headers(uint64_t(count) * kHeaderWords, 0), blob_off(count + 1, 0);

@@ -90,9 +90,8 @@ __device__ __forceinline__ uint64_t lookup_decoded(const View& v, const uint64_t
 // Bit reads inside one bucket's code.  The tree bits are read as 32-bit
 // little-endian words (bit k of the vector is bit k mod 32 of 32-bit word
 // k / 32, the same bits as the 64-bit layout), with positions relative to the
-// 32-bit word `t` that holds the code's first bit.  A bucket has at most 65535
-// keys and every index is below 2^36 and below 1024 times its node's expected
-// number of trials, so a bucket's code is far shorter than 2^32 bits and
+// 32-bit word `t` that holds the code's first bit.  A bucket's code takes about
+// two bits per key and the build rejects one that reaches 2^32 bits, so
 // positions fit 32-bit registers.  32-bit words make every mask, shift, find
 // and count a single instruction.
 __device__ __forceinline__ uint32_t code_bits(const uint32_t* __restrict__ t, uint32_t pos, uint32_t width) {

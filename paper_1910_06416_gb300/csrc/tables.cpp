@@ -130,8 +130,15 @@ int build_tables(uint32_t leaf, uint32_t extra, uint64_t mmax, Tables* T, std::s
     T->device_words[kTableWords * m + 1] =
         sh.unit | (static_cast<uint64_t>(sh.fanout) << 32) | (static_cast<uint64_t>(r) << 40);
     T->device_words[kTableWords * m + 2] = T->expected_trials[m];
-    T->device_words[kTableWords * m + 3] =
-        (sh.unit >= 2 ? ((1ull << 32) + sh.unit - 1) / sh.unit : 0) | (T->range[m] << 32);
+    // word 3, lower half: M = ceil(2^32 / unit), with which floor(v * M / 2^32)
+    // = floor(v / unit) for every v < m when (m - 1) * (M * unit - 2^32) < 2^32
+    // (always for m < 2^16); 0 where that fails, and the lookup divides
+    uint64_t magic = 0;
+    if (sh.unit >= 2) {
+      const uint64_t M = ((1ull << 32) + sh.unit - 1) / sh.unit;
+      if ((m - 1) * (M * sh.unit - (1ull << 32)) < (1ull << 32)) magic = M;
+    }
+    T->device_words[kTableWords * m + 3] = magic | (T->range[m] << 32);
   }
   return RECSPLIT_OK;
 }

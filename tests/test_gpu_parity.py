@@ -202,6 +202,23 @@ def test_offsets_that_decrease_are_rejected(rs, orc):
     assert b[100] == host_u64(empty)[0]
 
 
+@pytest.mark.parametrize("extra", [0, 2])
+def test_buckets_of_more_than_65536_keys(rs, orc, extra):
+    # b = 65535 and n = 2b: two buckets, the larger one above 2^16 keys (65731
+    # for this seed).  Its root split takes the search path that divides by
+    # the part size (the fixed-point reciprocal is exact only below 2^16).
+    n, b = 131070, 65535
+    keys = inputs.u64_keys(n, 20)
+    ref = orc.build_u64(keys, 8, b, threads=THREADS, extra=extra)
+    assert orc.header(ref)["mmax"] >= 65536
+    s = (rs.Structure.build_perfect_u64(dev_u64(keys), 8, b, extra) if extra
+         else gpu_build_u64(rs, keys, 8, b))
+    assert_same_blob(s.serialize(), ref)
+    got = gpu_lookup_u64(s, keys)
+    assert np.array_equal(got, orc.lookup_u64(ref, keys))
+    assert np.unique(got).shape[0] == n
+
+
 def test_results_do_not_depend_on_key_order(rs):
     keys = inputs.u64_keys(60000, 27)
     a = gpu_build_u64(rs, keys, 8, 100).serialize()
