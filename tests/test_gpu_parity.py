@@ -106,6 +106,26 @@ def test_byte_strings_with_unaligned_offsets(rs, orc):
     assert_same_blob(s.serialize(), ref)
 
 
+def test_long_byte_strings(rs, orc):
+    # lengths 8 .. 5000 (up to 625 eight-byte words per key) at every start
+    # alignment, plus the empty string; random bytes, so the keys are distinct
+    rng = np.random.default_rng(31)
+    lens = np.concatenate([[0, 8, 5000], rng.integers(8, 5001, 2997)]).astype(np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    data = rng.integers(0, 256, int(offsets[-1]), dtype=np.uint8)
+    ref = orc.build_bytes(data, offsets, 8, 100)
+    d = torch.from_numpy(data).cuda()
+    o = dev_u64(offsets)
+    s = rs.Structure.build_bytes(d, o, 8, 100)
+    assert_same_blob(s.serialize(), ref)
+    out = torch.empty(lens.shape[0], dtype=torch.int64, device="cuda")
+    s.lookup_bytes(d, o, out)
+    torch.cuda.synchronize()
+    got = host_u64(out)
+    assert np.array_equal(got, orc.lookup_bytes(ref, data, offsets))
+    assert np.array_equal(np.sort(got), np.arange(lens.shape[0], dtype=np.uint64))
+
+
 def test_host_buffers_give_the_same_structure(rs, orc):
     keys = inputs.u64_keys(50000, 21)
     ref = orc.build_u64(keys, 8, 100)
