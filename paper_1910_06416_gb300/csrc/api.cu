@@ -366,7 +366,7 @@ int recsplit_lookup_batch(const recsplit_t* const* hs, uint32_t count, const uin
   }
   bool any_range = false;
   for (uint32_t i = 0; i < count; i++) any_range |= views[i].extra != 0;
-  if ((rc = lookup_many(static_cast<const View*>(v.dev), static_cast<const uint32_t*>(d.dev),
+  if ((rc = lookup_many(static_cast<const View*>(v.dev), count, static_cast<const uint32_t*>(d.dev),
                         static_cast<const uint64_t*>(k.dev), q, static_cast<uint64_t*>(o.dev), s, any_range)))
     return rc;
   if (!dev) RS_CUDA(cudaMemcpyAsync(out, o.dev, q * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));

@@ -185,9 +185,11 @@ struct BuildOptions {
 int build_sets(const SetInput* sets, uint32_t count, const BuildOptions& opt, cudaStream_t s, Handle** out);
 // allow_scratch = false: allocate nothing (no per-batch decode of the lists)
 int lookup_structure(const Handle& h, const KeyInput& q, uint64_t* d_out, cudaStream_t s, bool allow_scratch = true);
-// any_range: some view has a leaf range extra (perfect, non-minimal variant)
-int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
-                cudaStream_t s, bool any_range = true);
+// Lookups of keys[i] in views[ids[i]] (count views); an id not below count
+// gives 2^64 - 1.  any_range: some view has a leaf range extra (perfect,
+// non-minimal variant)
+int lookup_many(const View* d_views, uint32_t count, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q,
+                uint64_t* d_out, cudaStream_t s, bool any_range = true);
 // Batched lookups over several structures with at least as many queries as
 // the structures have buckets: s_i, o_i of every bucket of every structure
 // are decoded into one pooled array *so (the caller frees it, stream-ordered,
@@ -195,8 +197,8 @@ int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_ke
 // part.  Otherwise, or if the memory is not available, *so stays null and the
 // views are unchanged (the lookups then select in the lists per query).
 int decode_views(View* views, uint32_t count, uint64_t q, cudaStream_t s, uint64_t** so);
-int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t* d_bytes, const uint64_t* d_offsets,
-                      uint64_t q, uint64_t* d_out, cudaStream_t s);
+int lookup_many_bytes(const View* d_views, uint32_t count, const uint32_t* d_ids, const uint8_t* d_bytes,
+                      const uint64_t* d_offsets, uint64_t q, uint64_t* d_out, cudaStream_t s);
 
 // Search launchers (search.cu).  A node's `depth` word holds its depth in
 // bits 0..7 and the parameter class (leaf size index) of its set in bits 8..15.

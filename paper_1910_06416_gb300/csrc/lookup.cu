@@ -231,29 +231,41 @@ __global__ void k_ef_decode_views(const View* __restrict__ views, const uint64_t
 
 // ANY_RANGE: some structure of the batch has a leaf range extra.  Bounded to
 // 32 registers like k_lookup_bytes (measured: 10.0 -> 8.6 ms per 10^8
-// batched lookups over 4096 structures).
+// batched lookups over 4096 structures).  A query whose structure id is not
+// below `count` gets the value 2^64 - 1 (no structure is read for it).
 template <bool ANY_RANGE>
-__global__ void __launch_bounds__(256, 8) k_lookup_many(const View* __restrict__ views, const uint32_t* __restrict__ ids,
-                              const uint64_t* __restrict__ keys, uint64_t q, uint64_t* __restrict__ out) {
+__global__ void __launch_bounds__(256, 8) k_lookup_many(const View* __restrict__ views, uint32_t count,
+                              const uint32_t* __restrict__ ids, const uint64_t* __restrict__ keys, uint64_t q,
+                              uint64_t* __restrict__ out) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t id = __ldg(ids + i);
+    if (id >= count) {
+      out[i] = ~0ull;
+      continue;
+    }
     uint64_t hi, lo;
     signature_u64(__ldg(keys + i), hi, lo);
-    const View& v = views[__ldg(ids + i)];
+    const View& v = views[id];
     out[i] = ANY_RANGE && v.extra ? (v.so ? lookup_decoded<true>(v, v.so, hi, lo) : lookup_one<true>(v, hi, lo))
                                   : (v.so ? lookup_decoded<false>(v, v.so, hi, lo) : lookup_one<false>(v, hi, lo));
   }
 }
 
-__global__ void k_lookup_many_bytes(const View* __restrict__ views, const uint32_t* __restrict__ ids,
+__global__ void k_lookup_many_bytes(const View* __restrict__ views, uint32_t count, const uint32_t* __restrict__ ids,
                                     const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ offsets,
                                     uint64_t q, uint64_t* __restrict__ out) {
   const uint64_t last = __ldg(offsets + q);  // the bytes span [0, offsets[q])
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < q; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t id = __ldg(ids + i);
+    if (id >= count) {
+      out[i] = ~0ull;
+      continue;
+    }
     const uint64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
     uint64_t hi, lo;
     const bool ok = o0 <= o1 && o1 <= last;  // else read as the empty string
     signature_bytes(bytes + (ok ? o0 : 0), ok ? o1 - o0 : 0, hi, lo);
-    const View& v = views[__ldg(ids + i)];
+    const View& v = views[id];
     out[i] = v.extra ? (v.so ? lookup_decoded<true>(v, v.so, hi, lo) : lookup_one<true>(v, hi, lo))
                      : (v.so ? lookup_decoded<false>(v, v.so, hi, lo) : lookup_one<false>(v, hi, lo));
   }
@@ -267,8 +279,8 @@ struct LookupRange {
   ~LookupRange() { nvtxRangePop(); }
 };
 
-int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t* d_bytes, const uint64_t* d_offsets,
-                      uint64_t q, uint64_t* d_out, cudaStream_t s) {
+int lookup_many_bytes(const View* d_views, uint32_t count, const uint32_t* d_ids, const uint8_t* d_bytes,
+                      const uint64_t* d_offsets, uint64_t q, uint64_t* d_out, cudaStream_t s) {
   if (q == 0) return RECSPLIT_OK;
   LookupRange range;
   int dev = 0, sms = 0;
@@ -277,13 +289,14 @@ int lookup_many_bytes(const View* d_views, const uint32_t* d_ids, const uint8_t*
   const int block = 256;
   const uint64_t want = (q + block - 1) / block;
   const unsigned grid = static_cast<unsigned>(want < uint64_t(sms) * 64 ? want : uint64_t(sms) * 64);
-  k_lookup_many_bytes<<<grid, block, 0, s>>>(d_views, d_ids, d_bytes, d_offsets, q, d_out);
+  k_lookup_many_bytes<<<grid, block, 0, s>>>(d_views, count, d_ids, d_bytes, d_offsets, q, d_out);
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;
 }
 
-int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q, uint64_t* d_out,
+int lookup_many(const View* d_views, uint32_t count, const uint32_t* d_ids, const uint64_t* d_keys, uint64_t q,
+                uint64_t* d_out,
                 cudaStream_t s, bool any_range) {
   if (q == 0) return RECSPLIT_OK;
   LookupRange range;
@@ -293,7 +306,8 @@ int lookup_many(const View* d_views, const uint32_t* d_ids, const uint64_t* d_ke
   const int block = 256;
   const uint64_t want = (q + block - 1) / block;
   const unsigned grid = static_cast<unsigned>(want < uint64_t(sms) * 64 ? want : uint64_t(sms) * 64);
-  (any_range ? k_lookup_many<true> : k_lookup_many<false>)<<<grid, block, 0, s>>>(d_views, d_ids, d_keys, q, d_out);
+  (any_range ? k_lookup_many<true> : k_lookup_many<false>)<<<grid, block, 0, s>>>(d_views, count, d_ids, d_keys, q,
+                                                                                  d_out);
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;

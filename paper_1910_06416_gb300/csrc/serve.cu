@@ -297,10 +297,11 @@ struct Server {
         pos += r.n;
       }
       if (kind == 1) cudaMemcpyAsync(d_offs, offs.data(), (q + 1) * 8, cudaMemcpyHostToDevice, sl);
-      rc = kind == 0 ? lookup_many(static_cast<View*>(d_views), static_cast<uint32_t*>(d_ids),
+      const uint32_t nviews = static_cast<uint32_t>(views.size());
+      rc = kind == 0 ? lookup_many(static_cast<View*>(d_views), nviews, static_cast<uint32_t*>(d_ids),
                                    static_cast<uint64_t*>(d_keys), q, static_cast<uint64_t*>(d_out), sl,
                                    /*any_range=*/false)  // the server builds minimal structures only
-                     : lookup_many_bytes(static_cast<View*>(d_views), static_cast<uint32_t*>(d_ids),
+                     : lookup_many_bytes(static_cast<View*>(d_views), nviews, static_cast<uint32_t*>(d_ids),
                                          static_cast<uint8_t*>(d_keys), static_cast<uint64_t*>(d_offs), q,
                                          static_cast<uint64_t*>(d_out), sl);
       pos = 0;

@@ -84,6 +84,30 @@ def test_small_batch_matches_oracle_and_single_builds(rs, orc):
             rs.recsplit_free(h)
 
 
+def test_batched_lookup_with_structure_ids_out_of_range(rs, orc):
+    # ids not below the number of structures give 2^64 - 1 and read nothing;
+    # the other queries are unaffected (device and host buffers, with and
+    # without the per-batch decode of the lists)
+    keys = [inputs.u64_keys(3000, 41), inputs.u64_keys(5000, 42)]
+    refs = [orc.build_u64(keys[0], 5, 5), orc.build_u64(keys[1], 8, 100)]
+    hs = [rs.Structure.build_u64(dev(keys[0]), 5, 5), rs.Structure.build_u64(dev(keys[1]), 8, 100)]
+    rng = np.random.default_rng(43)
+    for q in (50, 20000):
+        ids = rng.integers(0, 4, q).astype(np.uint32)
+        ids[:3] = [2, 0xFFFFFFFF, 1]
+        qk = np.array([keys[i % 2][rng.integers(0, keys[i % 2].shape[0])] for i in ids], dtype=np.uint64)
+        want = np.full(q, np.iinfo(np.uint64).max, dtype=np.uint64)
+        for i in (0, 1):
+            sel = ids == i
+            want[sel] = orc.lookup_u64(refs[i], qk[sel])
+        out = torch.empty(q, dtype=torch.int64, device="cuda")
+        rs.recsplit_lookup_batch([h.handle for h in hs], torch.from_numpy(ids.view(np.int32)).cuda(), dev(qk), out)
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
+        hout = np.zeros(q, dtype=np.uint64)
+        rs.recsplit_lookup_batch([h.handle for h in hs], ids, qk, hout)
+        assert np.array_equal(hout, want)
+
+
 def test_batch_structures_outlive_each_other(rs, orc):
     plan = [(5000, 5, 5, 11), (7000, 8, 100, 12)]
     keys = [inputs.u64_keys(n, sd) for n, _, _, sd in plan]
