@@ -138,7 +138,8 @@ int recsplit_build_batch(const recsplit_keyset_t* sets, uint32_t count, void* st
 
 /* Batched lookup over several structures: out[i] = lookup of keys[i] in
  * hs[ids[i]] (64-bit keys).  ids, keys and out: q entries each, device or
- * host memory (all three of one kind). */
+ * host memory (all three of one kind).  An id that is not below count gives
+ * out[i] = 2^64 - 1 (UINT64_MAX) and reads no structure. */
 int recsplit_lookup_batch(const recsplit_t* const* hs, uint32_t count, const uint32_t* ids, const uint64_t* keys,
                           uint64_t q, uint64_t* out, void* stream);
 
@@ -289,10 +290,11 @@ int recsplit_server_stats(recsplit_server_t* srv, recsplit_server_stats_t* st);
  * one fixed 16 MiB array in device memory that belongs to the library image
  * (every GPU that loads the library holds it until the process exits).  The
  * first call on a device looks up that array's device address, so make it
- * before any stream capture.  Every call shares the array: calls that overlap
- * on the GPU (other host threads or streams) race and must be serialised by
- * the caller.  q above the maximum fails with RECSPLIT_E_INVALID.  Returns
- * after the results are in out. */
+ * before any stream capture.  Every call on a device shares the array, so the
+ * library runs them one at a time (a host lock held from the copy of the keys
+ * until the results are in out): calls from several host threads are safe
+ * and wait for each other.  q above the maximum fails with RECSPLIT_E_INVALID.
+ * Returns after the results are in out. */
 int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
 
 /* Launch shapes of the seed searches for one leaf size.  They change only

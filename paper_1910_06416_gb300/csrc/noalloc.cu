@@ -27,10 +27,14 @@ static __device__ __align__(256) uint64_t g_stage[2 * kStaticMax];
 constexpr int kMaxDevices = 64;
 uint64_t* g_stage_addr[kMaxDevices] = {};
 std::mutex g_stage_mu;
+// One call at a time per device uses the array: held from the copy of the
+// keys until the results are back in the caller's buffer.
+std::mutex g_call_mu[kMaxDevices];
 
-int stage_address(uint64_t** out) {
+int stage_address(uint64_t** out, int* device) {
   int dev = 0;
   RS_CUDA(cudaGetDevice(&dev));
+  *device = dev;
   if (dev < 0 || dev >= kMaxDevices) return fail(RECSPLIT_E_INVALID, "device ordinal above 63");
   std::lock_guard<std::mutex> lock(g_stage_mu);
   if (!g_stage_addr[dev]) {
@@ -56,8 +60,10 @@ extern "C" int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* k
   if (q == 0) return RECSPLIT_OK;
   if (!keys || !out) return fail(RECSPLIT_E_INVALID, "keys or out is NULL");
   uint64_t* stage = nullptr;
-  int rc = stage_address(&stage);
+  int dev = 0;
+  int rc = stage_address(&stage, &dev);
   if (rc) return rc;
+  std::lock_guard<std::mutex> call(g_call_mu[dev]);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint64_t* d_keys = stage;
   uint64_t* d_out = stage + kStaticMax;

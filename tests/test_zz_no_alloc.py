@@ -6,6 +6,8 @@ structure, call after call, since both run the same lookup and every value
 is an exact integer.  This file is collected last so that a failure here
 cannot stop the other tests of a run.
 """
+import concurrent.futures as cf
+
 import numpy as np
 import pytest
 
@@ -55,3 +57,27 @@ def test_static_lookup_rejects_oversized_batches(rs):
     with pytest.raises(rs.RecSplitError) as e:
         rs.recsplit_lookup_u64_static(s.handle, big, out)
     assert e.value.code == rs.E_INVALID
+
+
+def test_static_lookups_from_several_host_threads(rs):
+    # the calls share one staging array; the library runs them one at a time,
+    # so every thread gets the results of its own keys
+    keys = inputs.u64_keys(100000, 35)
+    s = rs.Structure.build_u64(torch.from_numpy(keys.view(np.int64)).cuda(), 8, 100)
+    qs = [keys[inputs.query_indices(keys.shape[0], 200000 + 1000 * t, 36 + t)] for t in range(8)]
+    wants = []
+    for q in qs:
+        w = np.zeros(q.shape[0], dtype=np.uint64)
+        rs.recsplit_lookup_u64(s.handle, q, w)
+        wants.append(w)
+
+    def run(t):
+        got = np.zeros(qs[t].shape[0], dtype=np.uint64)
+        for _ in range(3):
+            rs.recsplit_lookup_u64_static(s.handle, qs[t], got)
+            if not np.array_equal(got, wants[t]):
+                return False
+        return True
+
+    with cf.ThreadPoolExecutor(8) as ex:
+        assert all(ex.map(run, range(8)))
