@@ -54,3 +54,45 @@ def test_binding_structs_match_the_header(tmp_path):
         assert layout[(cname, "size")] == C.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert layout[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def header_prototypes():
+    """name -> list of parameter type strings, from include/recsplit.h."""
+    import re
+    text = open(os.path.join(ROOT, "include", "recsplit.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(?:int|void|uint64_t|const char\s*\*)\s+(recsplit_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        args = " ".join(m.group(2).split())
+        params = [] if args in ("", "void") else [a.strip() for a in args.split(",")]
+        types = []
+        for a in params:
+            a = re.sub(r"\b[a-z_][a-z0-9_]*$", "", a).strip()  # drop the parameter name
+            types.append(a)
+        protos[m.group(1)] = types
+    return protos
+
+
+def ctype_of(decl):
+    if "*" in decl:
+        return "pointer"
+    return {"uint64_t": C.c_uint64, "uint32_t": C.c_uint32, "int": C.c_int, "size_t": C.c_size_t,
+            "int64_t": C.c_int64}[decl.replace("const ", "").strip()]
+
+
+def test_binding_argtypes_match_the_prototypes():
+    from paper_1910_06416_gb300 import build
+    build.build()
+    L = rs.lib()
+    protos = header_prototypes()
+    assert set(protos) == set(rs.header_functions())
+    for name, types in protos.items():
+        argtypes = getattr(L, name).argtypes
+        assert argtypes is not None, name
+        assert len(argtypes) == len(types), (name, types)
+        for t, a in zip(types, argtypes):
+            want = ctype_of(t)
+            if want == "pointer":
+                assert a is C.c_void_p or issubclass(a, C._Pointer) or a is C.c_char_p, (name, t, a)
+            else:
+                assert C.sizeof(a) == C.sizeof(want) and a(-1).value == want(-1).value, (name, t, a)
