@@ -174,6 +174,25 @@ def traffic_from_profiles(kernel_tag, source="search.cu", key="dram_bytes_per_la
         return None
 
 
+def counters_from_profiles(kernel_tag, source="search.cu"):
+    """Issue-slot and DRAM utilisation (percent, first captured launch) from an
+    ncu capture summary, if the kernel source has not changed since (else
+    None): which of the two limits the kernel."""
+    if traffic_from_profiles(kernel_tag, source) is None:
+        return None
+    want = {"smsp__issue_active.avg.pct_of_peak_sustained_active": "issue_active_pct",
+            "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed": "dram_throughput_pct"}
+    out = {}
+    for line in open(os.path.join(ROOT, "profiles", f"{kernel_tag}.md")):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] in want:
+            try:
+                out[want[cells[0]]] = float(cells[2])
+            except ValueError:
+                pass
+    return out or None
+
+
 def timed_repeats(fn, min_s=10.0, max_reps=100000):
     """Runs fn until at least min_s seconds have passed (at most max_reps
     times); returns (repetitions, seconds)."""
@@ -416,6 +435,8 @@ def run_ours(a):
                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                    "traffic": traffic_from_profiles(f"lookup_{tag}", "lookup.cu")},
     }
+    for name, src in (("leaf_search", "search.cu"), ("split_search", "search.cu"), ("lookup", "lookup.cu")):
+        rooflines[name]["ncu"] = counters_from_profiles(f"{name}_{tag}" if name != "lookup" else f"lookup_{tag}", src)
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
         if r["traffic"] is not None:
