@@ -80,6 +80,34 @@ def test_u64_structure_and_lookups_match_oracle(rs, orc, leaf, b, n, seed):
     assert st["n"] == n and st["num_codes"] == orc.header(ref)["codes"]
 
 
+def random_configs(count=40, seed=77):
+    # leaf sizes 1..12, bucket sizes log-uniform in [1, 3000], 0..6000 keys
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        leaf = int(rng.integers(1, 13))
+        b = int(np.floor(10 ** rng.uniform(0, np.log10(3001))))
+        n = int(rng.integers(0, 6001))
+        out.append((leaf, max(1, b), n, 1000 + k))
+    return out
+
+
+@pytest.mark.parametrize("extra", [0, 1, 3, 8])
+def test_random_small_configurations(rs, orc, extra):
+    # 120 drawn (leaf, bucket, n) points per leaf range extra; extra 0 is the
+    # minimal structure, the others the perfect, non-minimal variant
+    cfgs = random_configs(120, 77 + extra)
+    with cf.ThreadPoolExecutor(THREADS) as ex:
+        refs = list(ex.map(lambda c: orc.build_u64(inputs.u64_keys(c[2], c[3]), c[0], c[1], extra=extra), cfgs))
+    for (leaf, b, n, seed), ref in zip(cfgs, refs):
+        keys = inputs.u64_keys(n, seed)
+        s = (rs.Structure.build_perfect_u64(dev_u64(keys), leaf, b, extra) if extra
+             else gpu_build_u64(rs, keys, leaf, b))
+        assert_same_blob(s.serialize(), ref)
+        if n:
+            assert np.array_equal(gpu_lookup_u64(s, keys), orc.lookup_u64(ref, keys)), (leaf, b, n)
+
+
 @pytest.mark.parametrize("leaf,b,n", [(8, 100, 20000), (5, 5, 3000), (3, 1, 500), (12, 40, 1500)])
 def test_byte_string_structure_matches_oracle(rs, orc, leaf, b, n):
     bk = inputs.byte_keys(n, 1 + n)
