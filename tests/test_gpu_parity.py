@@ -108,6 +108,26 @@ def test_random_small_configurations(rs, orc, extra):
             assert np.array_equal(gpu_lookup_u64(s, keys), orc.lookup_u64(ref, keys)), (leaf, b, n)
 
 
+@pytest.mark.parametrize("extra", [0, 2])
+def test_random_byte_string_configurations(rs, orc, extra):
+    cfgs = random_configs(60, 177 + extra)
+    keysets = [inputs.byte_keys(n, seed) for _, _, n, seed in cfgs]
+    with cf.ThreadPoolExecutor(THREADS) as ex:
+        refs = list(ex.map(lambda i: orc.build_bytes(keysets[i].data, keysets[i].offsets, cfgs[i][0], cfgs[i][1],
+                                                     extra=extra), range(len(cfgs))))
+    for (leaf, b, n, _), bk, ref in zip(cfgs, keysets, refs):
+        data = torch.from_numpy(bk.data).cuda() if bk.data.shape[0] else torch.zeros(1, dtype=torch.uint8).cuda()
+        offs = dev_u64(bk.offsets)
+        s = (rs.Structure.build_perfect_bytes(data, offs, leaf, b, extra) if extra
+             else rs.Structure.build_bytes(data, offs, leaf, b))
+        assert_same_blob(s.serialize(), ref)
+        if n:
+            out = torch.empty(n, dtype=torch.int64, device="cuda")
+            s.lookup_bytes(data, offs, out)
+            torch.cuda.synchronize()
+            assert np.array_equal(host_u64(out), orc.lookup_bytes(ref, bk.data, bk.offsets)), (leaf, b, n)
+
+
 @pytest.mark.parametrize("leaf,b,n", [(8, 100, 20000), (5, 5, 3000), (3, 1, 500), (12, 40, 1500)])
 def test_byte_string_structure_matches_oracle(rs, orc, leaf, b, n):
     bk = inputs.byte_keys(n, 1 + n)
