@@ -108,6 +108,44 @@ def test_batched_lookup_with_structure_ids_out_of_range(rs, orc):
         assert np.array_equal(hout, want)
 
 
+def test_batch_mixing_byte_string_and_u64_sets(rs, orc):
+    # 40 sets: 64-bit keys or byte strings, leaf sizes {3, 5, 8, 12}, leaf
+    # range extras {0, 2} (8 parameter classes), 0..20000 keys each
+    rng = np.random.default_rng(51)
+    plan = []
+    for i in range(40):
+        plan.append((int(rng.integers(0, 20001)) if i % 9 else int(rng.integers(0, 3)),
+                     int(rng.choice([3, 5, 8, 12])), int(rng.choice([5, 9, 100, 1000])), int(rng.choice([0, 2])),
+                     bool(rng.integers(0, 2)), 500 + i))
+    data, sets = [], []
+    for n, leaf, b, e, is_bytes, seed in plan:
+        if is_bytes:
+            bk = inputs.byte_keys(n, seed)
+            d = torch.from_numpy(bk.data).cuda() if bk.data.shape[0] else torch.zeros(1, dtype=torch.uint8).cuda()
+            data.append(bk)
+            sets.append((d, dev(bk.offsets), leaf, b, {"leaf_extra": e}))
+        else:
+            k = inputs.u64_keys(n, seed)
+            data.append(k)
+            sets.append((dev(k), leaf, b, {"leaf_extra": e}))
+
+    def ref(i):
+        n, leaf, b, e, is_bytes, _ = plan[i]
+        if is_bytes:
+            return orc.build_bytes(data[i].data, data[i].offsets, leaf, b, threads=2, extra=e)
+        return orc.build_u64(data[i], leaf, b, threads=2, extra=e)
+
+    with cf.ThreadPoolExecutor(THREADS) as ex:
+        refs = list(ex.map(ref, range(len(plan))))
+    hs = rs.recsplit_build_batch(sets)
+    try:
+        for i, h in enumerate(hs):
+            assert np.array_equal(rs.recsplit_serialize(h), refs[i]), plan[i]
+    finally:
+        for h in hs:
+            rs.recsplit_free(h)
+
+
 def test_batch_structures_outlive_each_other(rs, orc):
     plan = [(5000, 5, 5, 11), (7000, 8, 100, 12)]
     keys = [inputs.u64_keys(n, sd) for n, _, _, sd in plan]
