@@ -303,7 +303,13 @@ def test_config_strings_1e7_leaf8_bucket100(rs, orc):
     bk = inputs.byte_keys(n, 1)
     data = torch.from_numpy(bk.data).cuda()
     offs = dev_u64(bk.offsets)
-    s = rs.Structure.build_bytes(data, offs, 8, 100)
+    # the launch shapes the benchmark times: it autotunes for this workload first
+    saved = rs.recsplit_get_tuning(8)
+    rs.recsplit_autotune(8, 100, n)
+    try:
+        s = rs.Structure.build_bytes(data, offs, 8, 100)
+    finally:
+        rs.recsplit_set_tuning(8, saved)
     gpu_blob = s.serialize()
     ref = orc.build_bytes(bk.data, bk.offsets, 8, 100, threads=THREADS)
     assert_same_blob(gpu_blob, ref)
