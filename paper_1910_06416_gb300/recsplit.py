@@ -155,13 +155,36 @@ def header_functions() -> list[str]:
     return sorted(set(re.findall(r"\b(recsplit_[a-z0-9_]+)\s*\(", text)))
 
 
-def _ptr(x):
-    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+def _ptr(x, itemsize=None):
+    """Data pointer of a torch tensor or numpy array (None -> NULL).  The
+    library reads and writes the elements as one dense array, so a strided
+    view, or elements of another size than the argument's (itemsize bytes),
+    raise ValueError instead of being misread."""
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous")
+        if itemsize is not None and x.element_size() != itemsize:
+            raise ValueError(f"expected {itemsize}-byte elements, got {x.element_size()}-byte {x.dtype}")
         return C.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array arguments must be C-contiguous")
+    if itemsize is not None and x.itemsize != itemsize:
+        raise ValueError(f"expected {itemsize}-byte elements, got {x.itemsize}-byte {x.dtype}")
     return x.ctypes.data_as(C.c_void_p)
+
+
+def _u64(x):
+    return _ptr(x, 8)
+
+
+def _u32(x):
+    return _ptr(x, 4)
+
+
+def _u8(x):
+    return _ptr(x, 1)
 
 
 def _stream(stream):
@@ -189,21 +212,21 @@ def _count(x) -> int:
 def recsplit_build_u64(keys, leaf_size: int, bucket_size: int, stream=None) -> int:
     """Build from 64-bit keys; returns the opaque handle (an int)."""
     h = C.c_void_p()
-    _check(lib().recsplit_build_u64(_ptr(keys), _count(keys), leaf_size, bucket_size, _stream(stream), C.byref(h)),
+    _check(lib().recsplit_build_u64(_u64(keys), _count(keys), leaf_size, bucket_size, _stream(stream), C.byref(h)),
            "recsplit_build_u64")
     return h.value
 
 
 def recsplit_build(keys, leaf_size: int, bucket_size: int, stream=None) -> int:
     h = C.c_void_p()
-    _check(lib().recsplit_build(_ptr(keys), _count(keys), leaf_size, bucket_size, _stream(stream), C.byref(h)),
+    _check(lib().recsplit_build(_u64(keys), _count(keys), leaf_size, bucket_size, _stream(stream), C.byref(h)),
            "recsplit_build")
     return h.value
 
 
 def recsplit_build_bytes(data, offsets, leaf_size: int, bucket_size: int, stream=None) -> int:
     h = C.c_void_p()
-    _check(lib().recsplit_build_bytes(_ptr(data), _ptr(offsets), _count(offsets) - 1, leaf_size, bucket_size,
+    _check(lib().recsplit_build_bytes(_u8(data), _u64(offsets), _count(offsets) - 1, leaf_size, bucket_size,
                                       _stream(stream), C.byref(h)), "recsplit_build_bytes")
     return h.value
 
@@ -211,7 +234,7 @@ def recsplit_build_bytes(data, offsets, leaf_size: int, bucket_size: int, stream
 def recsplit_build_perfect_u64(keys, leaf_size: int, bucket_size: int, leaf_extra: int, stream=None) -> int:
     """Perfect, non-minimal variant: leaves of m keys map into m + leaf_extra values."""
     h = C.c_void_p()
-    _check(lib().recsplit_build_perfect_u64(_ptr(keys), _count(keys), leaf_size, bucket_size, leaf_extra,
+    _check(lib().recsplit_build_perfect_u64(_u64(keys), _count(keys), leaf_size, bucket_size, leaf_extra,
                                             _stream(stream), C.byref(h)), "recsplit_build_perfect_u64")
     return h.value
 
@@ -219,14 +242,14 @@ def recsplit_build_perfect_u64(keys, leaf_size: int, bucket_size: int, leaf_extr
 def recsplit_build_perfect_bytes(data, offsets, leaf_size: int, bucket_size: int, leaf_extra: int,
                                  stream=None) -> int:
     h = C.c_void_p()
-    _check(lib().recsplit_build_perfect_bytes(_ptr(data), _ptr(offsets), _count(offsets) - 1, leaf_size,
+    _check(lib().recsplit_build_perfect_bytes(_u8(data), _u64(offsets), _count(offsets) - 1, leaf_size,
                                               bucket_size, leaf_extra, _stream(stream), C.byref(h)),
            "recsplit_build_perfect_bytes")
     return h.value
 
 
 def recsplit_lookup_u64(h: int, keys, out, stream=None) -> None:
-    _check(lib().recsplit_lookup_u64(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
+    _check(lib().recsplit_lookup_u64(C.c_void_p(h), _u64(keys), _count(keys), _u64(out), _stream(stream)),
            "recsplit_lookup_u64")
 
 
@@ -244,10 +267,10 @@ def recsplit_build_batch(sets, stream=None) -> list[int]:
             st = st[:-1]
         if len(st) == 3:
             keys, leaf, b = st
-            arr[i] = KeySet(_ptr(keys), None, None, _count(keys), leaf, b, extra, 0)
+            arr[i] = KeySet(_u64(keys), None, None, _count(keys), leaf, b, extra, 0)
         else:
             data, offs, leaf, b = st
-            arr[i] = KeySet(None, _ptr(data), _ptr(offs), _count(offs) - 1, leaf, b, extra, 0)
+            arr[i] = KeySet(None, _u8(data), _u64(offs), _count(offs) - 1, leaf, b, extra, 0)
     outs = (C.c_void_p * max(1, len(sets)))()
     _check(lib().recsplit_build_batch(C.cast(arr, C.c_void_p), len(sets), _stream(stream), C.cast(outs, C.c_void_p)),
            "recsplit_build_batch")
@@ -257,8 +280,8 @@ def recsplit_build_batch(sets, stream=None) -> list[int]:
 def recsplit_lookup_batch(handles, ids, keys, out, stream=None) -> None:
     """out[i] = lookup of keys[i] in handles[ids[i]]."""
     hs = (C.c_void_p * max(1, len(handles)))(*handles)
-    _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _ptr(ids), _ptr(keys), _count(keys),
-                                       _ptr(out), _stream(stream)), "recsplit_lookup_batch")
+    _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _u32(ids), _u64(keys), _count(keys),
+                                       _u64(out), _stream(stream)), "recsplit_lookup_batch")
 
 
 # ---------------------------------------------------------------- failures
@@ -304,14 +327,14 @@ def recsplit_server_destroy(srv: int) -> None:
 
 def recsplit_server_submit_build_u64(srv: int, keys, leaf_size: int, bucket_size: int) -> int:
     rid = C.c_uint64()
-    _check(lib().recsplit_server_submit_build_u64(C.c_void_p(srv), _ptr(keys), _count(keys), leaf_size, bucket_size,
+    _check(lib().recsplit_server_submit_build_u64(C.c_void_p(srv), _u64(keys), _count(keys), leaf_size, bucket_size,
                                                   C.byref(rid)), "recsplit_server_submit_build_u64")
     return rid.value
 
 
 def recsplit_server_submit_build_bytes(srv: int, data, offsets, leaf_size: int, bucket_size: int) -> int:
     rid = C.c_uint64()
-    _check(lib().recsplit_server_submit_build_bytes(C.c_void_p(srv), _ptr(data), _ptr(offsets), _count(offsets) - 1,
+    _check(lib().recsplit_server_submit_build_bytes(C.c_void_p(srv), _u8(data), _u64(offsets), _count(offsets) - 1,
                                                     leaf_size, bucket_size, C.byref(rid)),
            "recsplit_server_submit_build_bytes")
     return rid.value
@@ -319,15 +342,15 @@ def recsplit_server_submit_build_bytes(srv: int, data, offsets, leaf_size: int, 
 
 def recsplit_server_submit_lookup_u64(srv: int, structure_id: int, keys, out) -> int:
     rid = C.c_uint64()
-    _check(lib().recsplit_server_submit_lookup_u64(C.c_void_p(srv), structure_id, _ptr(keys), _count(keys), _ptr(out),
+    _check(lib().recsplit_server_submit_lookup_u64(C.c_void_p(srv), structure_id, _u64(keys), _count(keys), _u64(out),
                                                    C.byref(rid)), "recsplit_server_submit_lookup_u64")
     return rid.value
 
 
 def recsplit_server_submit_lookup_bytes(srv: int, structure_id: int, data, offsets, out) -> int:
     rid = C.c_uint64()
-    _check(lib().recsplit_server_submit_lookup_bytes(C.c_void_p(srv), structure_id, _ptr(data), _ptr(offsets),
-                                                     _count(offsets) - 1, _ptr(out), C.byref(rid)),
+    _check(lib().recsplit_server_submit_lookup_bytes(C.c_void_p(srv), structure_id, _u8(data), _u64(offsets),
+                                                     _count(offsets) - 1, _u64(out), C.byref(rid)),
            "recsplit_server_submit_lookup_bytes")
     return rid.value
 
@@ -361,17 +384,17 @@ STATIC_LOOKUP_MAX = 1 << 20
 
 def recsplit_lookup_u64_static(h: int, keys, out, stream=None) -> None:
     """Lookup that allocates no device memory (at most STATIC_LOOKUP_MAX keys)."""
-    _check(lib().recsplit_lookup_u64_static(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
+    _check(lib().recsplit_lookup_u64_static(C.c_void_p(h), _u64(keys), _count(keys), _u64(out), _stream(stream)),
            "recsplit_lookup_u64_static")
 
 
 def recsplit_lookup(h: int, keys, out, stream=None) -> None:
-    _check(lib().recsplit_lookup(C.c_void_p(h), _ptr(keys), _count(keys), _ptr(out), _stream(stream)),
+    _check(lib().recsplit_lookup(C.c_void_p(h), _u64(keys), _count(keys), _u64(out), _stream(stream)),
            "recsplit_lookup")
 
 
 def recsplit_lookup_bytes(h: int, data, offsets, out, stream=None) -> None:
-    _check(lib().recsplit_lookup_bytes(C.c_void_p(h), _ptr(data), _ptr(offsets), _count(offsets) - 1, _ptr(out),
+    _check(lib().recsplit_lookup_bytes(C.c_void_p(h), _u8(data), _u64(offsets), _count(offsets) - 1, _u64(out),
                                        _stream(stream)), "recsplit_lookup_bytes")
 
 
@@ -413,13 +436,13 @@ def recsplit_last_error() -> str:
 
 def recsplit_golomb_rice_params(leaf_size: int, m_hi: int) -> np.ndarray:
     out = np.zeros(m_hi + 1, dtype=np.uint8)
-    _check(lib().recsplit_golomb_rice_params(leaf_size, m_hi, _ptr(out)), "recsplit_golomb_rice_params")
+    _check(lib().recsplit_golomb_rice_params(leaf_size, m_hi, _u8(out)), "recsplit_golomb_rice_params")
     return out
 
 
 def recsplit_golomb_rice_params_extra(leaf_size: int, leaf_extra: int, m_hi: int) -> np.ndarray:
     out = np.zeros(m_hi + 1, dtype=np.uint8)
-    _check(lib().recsplit_golomb_rice_params_extra(leaf_size, leaf_extra, m_hi, _ptr(out)),
+    _check(lib().recsplit_golomb_rice_params_extra(leaf_size, leaf_extra, m_hi, _u8(out)),
            "recsplit_golomb_rice_params_extra")
     return out
 

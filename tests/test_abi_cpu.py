@@ -99,3 +99,24 @@ def test_tuning_shapes_are_validated(rs):
         assert e.value.code == rs.E_INVALID
     with pytest.raises(rs.RecSplitError):
         rs.recsplit_get_tuning(25)
+
+
+def test_binding_rejects_strided_and_mistyped_arrays(rs):
+    # checked before the library is called: the C ABI reads dense arrays of
+    # fixed-size elements
+    keys = np.arange(20, dtype=np.uint64)
+    with pytest.raises(ValueError):
+        rs.recsplit_build_u64(keys[::2], 5, 5)
+    with pytest.raises(ValueError):
+        rs.recsplit_build_u64(keys.astype(np.uint32), 5, 5)
+    data = np.zeros(16, dtype=np.uint8)
+    with pytest.raises(ValueError):
+        rs.recsplit_build_bytes(data, np.array([0, 8, 16], dtype=np.int32), 5, 5)
+    with pytest.raises(ValueError):
+        rs.recsplit_lookup_batch([0], np.zeros(4, dtype=np.uint64), np.zeros(4, dtype=np.uint64),
+                                 np.zeros(4, dtype=np.uint64))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        rs.recsplit_build_u64(torch.arange(20, dtype=torch.int64)[::2], 5, 5)
+    with pytest.raises(ValueError):
+        rs.recsplit_build_u64(torch.arange(20, dtype=torch.int32), 5, 5)
