@@ -161,9 +161,15 @@ int recsplit_lookup(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint6
  * otherwise cap must be at least that size.  Synchronises with the device. */
 int recsplit_serialize(const recsplit_t* h, void* buf, size_t cap, size_t* len);
 
-/* Structure from a serialized buffer in host memory (copied).  The header
- * and the section sizes are checked (RECSPLIT_E_INVALID); the codes are not,
- * so load only buffers written by recsplit_serialize. */
+/* Structure from a serialized buffer in host memory (copied).  Before
+ * anything is copied to the device, the host checks everything a lookup's
+ * reads depend on: the header and section sizes, both Elias-Fano lists and
+ * their inventories (Sec. 6.3, 7.4), every bucket's size against the
+ * header, and every bucket's code length and unary one bits against its tree
+ * (Sec. 6.2); a structure that fails fails with RECSPLIT_E_INVALID.  The
+ * fixed parts of the codes cannot be checked (any value is an index): a
+ * damaged one makes lookups return other values, never read outside the
+ * structure. */
 int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t** out);
 
 /* Summary figures of a structure (host only, no device work). */
@@ -294,7 +300,8 @@ int recsplit_server_stats(recsplit_server_t* srv, recsplit_server_stats_t* st);
  * library runs them one at a time (a host lock held from the copy of the keys
  * until the results are in out): calls from several host threads are safe
  * and wait for each other.  q above the maximum fails with RECSPLIT_E_INVALID.
- * Returns after the results are in out. */
+ * Every call, failed ones included, synchronizes `stream` before it returns
+ * (the results are in out on success). */
 int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
 
 /* Launch shapes of the seed searches for one leaf size.  They change only

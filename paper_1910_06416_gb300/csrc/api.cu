@@ -1,8 +1,10 @@
 // C ABI entry points (include/recsplit.h): argument checks, host/device
 // buffer staging, serialization and error reporting.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <string>
 #include <vector>
@@ -467,10 +469,35 @@ int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t**
   const Layout L = layout_of(H);
   if (L.total != H[H_WORDS] || L.total * sizeof(uint64_t) != len)
     return fail(RECSPLIT_E_INVALID, "size does not match the header");
-  Tables T;
+  // everything a lookup reads is checked before the structure is loaded:
+  // lists, inventories, sizes and codes (validate.cpp)
+  const uint64_t* words = static_cast<const uint64_t*>(buf);
+  std::vector<uint64_t> s_list, o_list;
   std::string err;
-  int rc = build_tables(header_leaf(H), header_extra(H), H[H_MMAX], &T, &err);
+  int rc;
+  try {
+    if ((rc = check_lists(words, H, L, &s_list, &o_list, &err))) return fail(rc, err);
+    uint64_t widest = 0;  // largest bucket output range (its size when e = 0)
+    for (uint64_t i = 0; i < H[H_NB]; i++) widest = std::max(widest, s_list[i + 1] - s_list[i]);
+    if (header_extra(H) == 0 ? H[H_MMAX] != widest : H[H_MMAX] > widest)
+      return fail(RECSPLIT_E_INVALID, "structure check failed: the largest bucket does not match the lists");
+    const uint64_t total = s_list[H[H_NB]];
+    if (header_extra(H) == 0 ? total != H[H_N] : total < H[H_N])
+      return fail(RECSPLIT_E_INVALID, "structure check failed: the prefix sums do not end at the key count");
+  } catch (const std::bad_alloc&) {
+    return fail(RECSPLIT_E_NOMEM, "host memory for the structure check");
+  }
+  Tables T;
+  try {
+    rc = build_tables(header_leaf(H), header_extra(H), H[H_MMAX], &T, &err);
+    if (!rc) rc = check_codes(words, H, L, T, header_extra(H), s_list, o_list, &err);
+  } catch (const std::bad_alloc&) {
+    return fail(RECSPLIT_E_NOMEM, "host memory for the structure check");
+  }
   if (rc) return fail(rc, err);
+  const uint64_t range_total = H[H_NB] ? s_list[H[H_NB]] : 0;
+  std::vector<uint64_t>().swap(s_list);
+  std::vector<uint64_t>().swap(o_list);
   Handle* h = new Handle();
   std::memcpy(h->header, H, sizeof(H));
   h->layout = L;
@@ -494,23 +521,8 @@ int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t**
     return rc;
   }
   h->ncodes = H[H_CODES];
-  // output range: the last element of the first Elias-Fano list, whose
-  // upper bits end the upper-bits array (Sec. 7.4), plus the rescaling
-  {
-    const uint64_t* w = static_cast<const uint64_t*>(buf);
-    const uint64_t nb = H[H_NB], la = H[H_LOW_A];
-    uint64_t low = 0;
-    if (la) {
-      const uint64_t pos = nb * (la + H[H_LOW_B]);
-      const uint64_t* lower = w + L.lower;
-      low = lower[pos >> 6] >> (pos & 63);
-      if ((pos & 63) + la > 64) low |= lower[(pos >> 6) + 1] << (64 - (pos & 63));
-      low &= la == 64 ? ~0ull : ((1ull << la) - 1);
-    }
-    const uint64_t xa_last = H[H_UP_A] >= nb + 1 ? ((H[H_UP_A] - 1 - nb) << la) | low : 0;
-    h->range_size = nb ? xa_last + static_cast<uint64_t>(static_cast<int64_t>(nb) * static_cast<int64_t>(H[H_DELTA_A]))
-                       : 0;
-  }
+  // output range: the last element of the first Elias-Fano list
+  h->range_size = range_total;
   *out = reinterpret_cast<recsplit_t*>(h);
   return RECSPLIT_OK;
 }

@@ -81,6 +81,14 @@ struct Tables {
 // w3 = ceil(2^32 / unit) | subtree output range << 32.
 int build_tables(uint32_t leaf, uint32_t extra, uint64_t mmax, Tables* out, std::string* err);
 
+// Host-side check of a serialized structure (validate.cpp): the lists and
+// their inventories (s, o: decoded prefix sums of the bucket output ranges
+// and bit offsets), then every bucket's codes against the tables.
+int check_lists(const uint64_t* w, const uint64_t* H, const Layout& L, std::vector<uint64_t>* s,
+                std::vector<uint64_t>* o, std::string* err);
+int check_codes(const uint64_t* w, const uint64_t* H, const Layout& L, const Tables& T, uint32_t extra,
+                const std::vector<uint64_t>& s, const std::vector<uint64_t>& o, std::string* err);
+
 // ---------------------------------------------------------------- handle
 // Device memory released when the last structure that uses it is freed
 // (the structures of one batched build share one arena).
@@ -110,6 +118,7 @@ struct View {
   const uint16_t* subs;
   const uint64_t* table;  // kTableWords words per size
   const uint64_t* so;  // s_i, o_i of every bucket decoded beforehand, or null
+  uint64_t tree_words32;  // 32-bit words of the tree section (code scans stop there)
   uint64_t mmax;       // largest bucket (the tables cover sizes 0 .. mmax)
   uint32_t extra;      // leaf range extra (0: minimal)
   uint64_t nb;

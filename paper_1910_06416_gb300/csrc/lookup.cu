@@ -101,10 +101,17 @@ __device__ __forceinline__ uint32_t code_bits(const uint32_t* __restrict__ t, ui
   return __funnelshift_r(lo, hi, o) & ((1u << width) - 1);  // width <= 31
 }
 
-__device__ __forceinline__ uint32_t code_next_one(const uint32_t* __restrict__ t, uint32_t pos) {
+// Scans stop at `end`, the 32-bit words from t to the end of the tree
+// section, and then return 2^32 - 1: the structure check of deserialize
+// already guarantees that every bucket's unary part holds its codes' one
+// bits, so this only bounds the reads.
+__device__ __forceinline__ uint32_t code_next_one(const uint32_t* __restrict__ t, uint32_t pos, uint32_t end) {
   uint32_t w = pos >> 5;
   uint32_t word = __ldg(t + w) & (~0u << (pos & 31));
-  while (!word) word = __ldg(t + (++w));
+  while (!word) {
+    if (++w >= end) return ~0u;
+    word = __ldg(t + w);
+  }
   return (w << 5) + static_cast<uint32_t>(__ffs(word) - 1);
 }
 
@@ -121,14 +128,16 @@ __device__ __forceinline__ uint32_t select_in_word32(uint32_t w, uint32_t k) {
   return pos + (k >= (w & 1u) ? 1u : 0u);
 }
 
-__device__ __forceinline__ uint32_t code_select(const uint32_t* __restrict__ t, uint32_t pos, uint32_t rank) {
+__device__ __forceinline__ uint32_t code_select(const uint32_t* __restrict__ t, uint32_t pos, uint32_t rank,
+                                                uint32_t end) {
   uint32_t w = pos >> 5;
   uint32_t word = __ldg(t + w) & (~0u << (pos & 31));
   for (;;) {
     const uint32_t c = __popc(word);
     if (rank < c) break;
     rank -= c;
-    word = __ldg(t + (++w));
+    if (++w >= end) return ~0u;
+    word = __ldg(t + w);
   }
   return (w << 5) + select_in_word32(word, rank);
 }
@@ -139,6 +148,8 @@ template <bool RANGE>
 __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
   const uint32_t extra = RANGE ? v.extra : 0;
   const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
+  const uint64_t left = v.tree_words32 - (o >> 5);
+  const uint32_t end = left < 0xFFFFFFFFull ? static_cast<uint32_t>(left) : 0xFFFFFFFFu;
   uint32_t fixed = static_cast<uint32_t>(o & 31);
   uint32_t c = 0;
   const uint64_t xpre = pre_key(lo);
@@ -152,7 +163,8 @@ __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t
     const uint32_t unit = static_cast<uint32_t>(tw.y);
     const uint32_t low = code_bits(t, fixed, r);
     fixed += r;
-    const uint32_t one = code_next_one(t, unary);
+    const uint32_t one = code_next_one(t, unary, end);
+    if (one == ~0u) return ~0ull;
     const uint64_t seed = (uint64_t(one - unary) << r) | low;
     unary = one + 1;
     if (fanout == 0) return s0 + c + phi_pre(xpre, family_key(seed, depth), m + extra);
@@ -165,7 +177,11 @@ __device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t
       const ulonglong2 tu = part + 1 < fanout ? tn : __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * unit));
       fixed += part * static_cast<uint32_t>(tu.x);
       const uint32_t skip = part * static_cast<uint32_t>(tu.x >> 32);
-      if (skip) unary = code_select(t, unary, skip - 1) + 1;
+      if (skip) {
+        const uint32_t at = code_select(t, unary, skip - 1, end);
+        if (at == ~0u) return ~0ull;
+        unary = at + 1;
+      }
       // keys (or, with a leaf range extra, output ranges) of the siblings left behind
       c += extra ? static_cast<uint32_t>(part * node_range(v, unit)) : part * unit;
     }
@@ -366,6 +382,7 @@ View make_view(const Handle& h) {
   v.anchors = h.d_blob + h.layout.anchors;
   v.subs = reinterpret_cast<const uint16_t*>(h.d_blob + h.layout.subs);
   v.table = h.d_table;
+  v.tree_words32 = 2 * words_of_bits(H[H_TBITS]);
   v.nb = H[H_NB];
   v.beta = H[H_BETA];
   v.delta_a = static_cast<int64_t>(H[H_DELTA_A]);

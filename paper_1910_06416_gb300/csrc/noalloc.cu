@@ -73,8 +73,15 @@ extern "C" int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* k
   KeyInput in;
   in.u64 = d_keys;
   in.n = q;
-  if ((rc = lookup_structure(*reinterpret_cast<const Handle*>(h), in, d_out, s, /*allow_scratch=*/false))) return rc;
-  RS_CUDA(cudaMemcpyAsync(out, d_out, q * sizeof(uint64_t), cudaMemcpyDefault, s));
-  RS_CUDA(cudaStreamSynchronize(s));
+  if ((rc = lookup_structure(*reinterpret_cast<const Handle*>(h), in, d_out, s, /*allow_scratch=*/false))) {
+    // the copy of the keys may still be queued: wait for it before the lock
+    // is released, so that the next call cannot overwrite the array under it
+    cudaStreamSynchronize(s);
+    return rc;
+  }
+  const cudaError_t e = cudaMemcpyAsync(out, d_out, q * sizeof(uint64_t), cudaMemcpyDefault, s);
+  const cudaError_t w = cudaStreamSynchronize(s);  // also on a failed copy: nothing stays queued on the array
+  if (e != cudaSuccess) return cuda_fail(e, "copy of the lookup results");
+  if (w != cudaSuccess) return cuda_fail(w, "cudaStreamSynchronize");
   return RECSPLIT_OK;
 }

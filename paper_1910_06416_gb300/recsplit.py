@@ -208,6 +208,27 @@ def _count(x) -> int:
     return int(x.shape[0])
 
 
+def _numel(x) -> int:
+    return int(x.numel()) if hasattr(x, "numel") else int(x.size)
+
+
+def _out(out, q: int, name: str = "out"):
+    """Pointer of an output array that must hold at least q elements: the
+    library writes q results, so a shorter array raises ValueError before the
+    call instead of being written past its end."""
+    if out is None:
+        raise ValueError(f"{name} is required")
+    if _numel(out) < q:
+        raise ValueError(f"{name} holds {_numel(out)} elements, fewer than the {q} queries")
+    return _u64(out)
+
+
+def _ids(ids, q: int):
+    if ids is None or _numel(ids) < q:
+        raise ValueError(f"ids must hold at least the {q} structure ids of the queries")
+    return _u32(ids)
+
+
 # ---------------------------------------------------------------- C names
 def recsplit_build_u64(keys, leaf_size: int, bucket_size: int, stream=None) -> int:
     """Build from 64-bit keys; returns the opaque handle (an int)."""
@@ -249,7 +270,8 @@ def recsplit_build_perfect_bytes(data, offsets, leaf_size: int, bucket_size: int
 
 
 def recsplit_lookup_u64(h: int, keys, out, stream=None) -> None:
-    _check(lib().recsplit_lookup_u64(C.c_void_p(h), _u64(keys), _count(keys), _u64(out), _stream(stream)),
+    q = _count(keys)
+    _check(lib().recsplit_lookup_u64(C.c_void_p(h), _u64(keys), q, _out(out, q), _stream(stream)),
            "recsplit_lookup_u64")
 
 
@@ -280,8 +302,9 @@ def recsplit_build_batch(sets, stream=None) -> list[int]:
 def recsplit_lookup_batch(handles, ids, keys, out, stream=None) -> None:
     """out[i] = lookup of keys[i] in handles[ids[i]]."""
     hs = (C.c_void_p * max(1, len(handles)))(*handles)
-    _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _u32(ids), _u64(keys), _count(keys),
-                                       _u64(out), _stream(stream)), "recsplit_lookup_batch")
+    q = _count(keys)
+    _check(lib().recsplit_lookup_batch(C.cast(hs, C.c_void_p), len(handles), _ids(ids, q), _u64(keys), q,
+                                       _out(out, q), _stream(stream)), "recsplit_lookup_batch")
 
 
 # ---------------------------------------------------------------- failures
@@ -342,15 +365,17 @@ def recsplit_server_submit_build_bytes(srv: int, data, offsets, leaf_size: int, 
 
 def recsplit_server_submit_lookup_u64(srv: int, structure_id: int, keys, out) -> int:
     rid = C.c_uint64()
-    _check(lib().recsplit_server_submit_lookup_u64(C.c_void_p(srv), structure_id, _u64(keys), _count(keys), _u64(out),
+    q = _count(keys)
+    _check(lib().recsplit_server_submit_lookup_u64(C.c_void_p(srv), structure_id, _u64(keys), q, _out(out, q),
                                                    C.byref(rid)), "recsplit_server_submit_lookup_u64")
     return rid.value
 
 
 def recsplit_server_submit_lookup_bytes(srv: int, structure_id: int, data, offsets, out) -> int:
     rid = C.c_uint64()
+    q = _count(offsets) - 1
     _check(lib().recsplit_server_submit_lookup_bytes(C.c_void_p(srv), structure_id, _u8(data), _u64(offsets),
-                                                     _count(offsets) - 1, _u64(out), C.byref(rid)),
+                                                     q, _out(out, q), C.byref(rid)),
            "recsplit_server_submit_lookup_bytes")
     return rid.value
 
@@ -384,17 +409,20 @@ STATIC_LOOKUP_MAX = 1 << 20
 
 def recsplit_lookup_u64_static(h: int, keys, out, stream=None) -> None:
     """Lookup that allocates no device memory (at most STATIC_LOOKUP_MAX keys)."""
-    _check(lib().recsplit_lookup_u64_static(C.c_void_p(h), _u64(keys), _count(keys), _u64(out), _stream(stream)),
+    q = _count(keys)
+    _check(lib().recsplit_lookup_u64_static(C.c_void_p(h), _u64(keys), q, _out(out, q), _stream(stream)),
            "recsplit_lookup_u64_static")
 
 
 def recsplit_lookup(h: int, keys, out, stream=None) -> None:
-    _check(lib().recsplit_lookup(C.c_void_p(h), _u64(keys), _count(keys), _u64(out), _stream(stream)),
+    q = _count(keys)
+    _check(lib().recsplit_lookup(C.c_void_p(h), _u64(keys), q, _out(out, q), _stream(stream)),
            "recsplit_lookup")
 
 
 def recsplit_lookup_bytes(h: int, data, offsets, out, stream=None) -> None:
-    _check(lib().recsplit_lookup_bytes(C.c_void_p(h), _u8(data), _u64(offsets), _count(offsets) - 1, _u64(out),
+    q = _count(offsets) - 1
+    _check(lib().recsplit_lookup_bytes(C.c_void_p(h), _u8(data), _u64(offsets), q, _out(out, q),
                                        _stream(stream)), "recsplit_lookup_bytes")
 
 

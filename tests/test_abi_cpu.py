@@ -120,3 +120,26 @@ def test_binding_rejects_strided_and_mistyped_arrays(rs):
         rs.recsplit_build_u64(torch.arange(20, dtype=torch.int64)[::2], 5, 5)
     with pytest.raises(ValueError):
         rs.recsplit_build_u64(torch.arange(20, dtype=torch.int32), 5, 5)
+
+
+def test_binding_rejects_outputs_shorter_than_the_queries(rs):
+    # the library writes one result per query: a shorter output array would
+    # be written past its end, so the binding raises before calling it
+    keys = np.arange(8, dtype=np.uint64)
+    short = np.zeros(7, dtype=np.uint64)
+    data = np.zeros(64, dtype=np.uint8)
+    offs = np.arange(0, 72, 8, dtype=np.uint64)  # 8 strings
+    for call in (lambda: rs.recsplit_lookup_u64(0, keys, short),
+                 lambda: rs.recsplit_lookup(0, keys, short),
+                 lambda: rs.recsplit_lookup_u64_static(0, keys, short),
+                 lambda: rs.recsplit_lookup_bytes(0, data, offs, short),
+                 lambda: rs.recsplit_lookup_batch([0], np.zeros(8, dtype=np.uint32), keys, short),
+                 lambda: rs.recsplit_lookup_batch([0], np.zeros(7, dtype=np.uint32), keys, np.zeros(8, np.uint64)),
+                 lambda: rs.recsplit_server_submit_lookup_u64(0, 1, keys, short),
+                 lambda: rs.recsplit_server_submit_lookup_bytes(0, 1, data, offs, short),
+                 lambda: rs.recsplit_lookup_u64(0, keys, None)):
+        with pytest.raises(ValueError):
+            call()
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        rs.recsplit_lookup_u64(0, keys, torch.zeros(7, dtype=torch.int64))

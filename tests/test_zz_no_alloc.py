@@ -28,14 +28,17 @@ def rs():
     return rs
 
 
-def test_static_lookup_equals_allocating_lookup_twice(rs):
+def test_static_lookup_equals_allocating_lookup_twice(rs, orc):
     keys = inputs.u64_keys(200000, 31)
     s = rs.Structure.build_u64(torch.from_numpy(keys.view(np.int64)).cuda(), 8, 100)
+    ref = orc.build_u64(keys, 8, 100)
     members = keys[inputs.query_indices(keys.shape[0], 300000, 32)]
     others = inputs.splitmix64(33, 50000)
     for q in (members, others, members[:rs.STATIC_LOOKUP_MAX]):
         want = np.zeros(q.shape[0], dtype=np.uint64)
         rs.recsplit_lookup_u64(s.handle, q, want)
+        # and directly against the oracle's lookup on its own structure
+        assert np.array_equal(want, orc.lookup_u64(ref, q))
         for _ in range(2):  # two calls in a row share the staging array
             got = np.full(q.shape[0], 7, dtype=np.uint64)
             rs.recsplit_lookup_u64_static(s.handle, q, got)
@@ -81,3 +84,27 @@ def test_static_lookups_from_several_host_threads(rs):
 
     with cf.ThreadPoolExecutor(8) as ex:
         assert all(ex.map(run, range(8)))
+
+
+def test_static_lookup_makes_no_device_allocation(rs, orc):
+    # the next device allocation of the library on this thread is made to
+    # fail (on the host, as if the device were out of memory): the
+    # allocation-free lookup must still succeed, while an allocating lookup
+    # that decodes the bucket lists per batch fails
+    keys = inputs.u64_keys(50000, 37)
+    s = rs.Structure.build_u64(keys, 8, 100)
+    q = keys[inputs.query_indices(keys.shape[0], 20000, 38)]
+    want = orc.lookup_u64(orc.build_u64(keys, 8, 100), q)
+    rs.recsplit_inject_alloc_failure(0)
+    try:
+        for _ in range(2):
+            got = np.zeros(q.shape[0], dtype=np.uint64)
+            rs.recsplit_lookup_u64_static(s.handle, q, got)
+            assert np.array_equal(got, want)
+        # still armed: the allocating lookup with host buffers stages them in
+        # device memory it allocates, and fails
+        with pytest.raises(rs.RecSplitError) as e:
+            rs.recsplit_lookup_u64(s.handle, q, np.zeros(q.shape[0], dtype=np.uint64))
+        assert e.value.code == rs.E_NOMEM
+    finally:
+        rs.recsplit_inject_alloc_failure(-1)
