@@ -928,8 +928,11 @@ int orc_decode_bucket(const uint64_t* blob, uint64_t b, uint64_t* seeds, uint64_
   }
   *count = k;
   free(stack);
+  /* the code must end exactly where the next bucket's begins (checked
+   * before the tables it reads are released) */
+  const int ok = upos == o1 && fpos == o0 + (m < 2 ? 0 : t.fbits[m]);
   orc_tables_free(&t);
-  return (upos == o1 && fpos == o0 + (m < 2 ? 0 : t.fbits[m])) ? ORC_OK : ORC_E_INVALID;
+  return ok ? ORC_OK : ORC_E_INVALID;
 }
 
 typedef struct {
