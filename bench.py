@@ -54,6 +54,8 @@ def parse():
                     help="strings: byte-string keys (default workload); u64: 64-bit keys (seed 0 for leaf 5, "
                          "seed 2 otherwise); batch: 4096 sets of log-uniform sizes with mixed leaf/bucket sizes")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the space-optimal (l=16, b=2000) and batched (4096 sets) entries of the default run")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
@@ -193,6 +195,20 @@ def counters_from_profiles(kernel_tag, source="search.cu"):
     return out or None
 
 
+def tuned_shapes(rs, leaf, bucket, sample, stream):
+    """Launch shapes for (GPU model, leaf size, bucket size): the persistent
+    tuning cache's entry if it has one, else the autotuner's on a seeded
+    synthetic sample of `sample` keys (then cached).  Shapes change only the
+    speed of a build, never its result."""
+    import torch
+    from paper_1910_06416_gb300 import tuning_cache
+    path = os.environ.get("RECSPLIT_TUNING_CACHE", tuning_cache.DEFAULT_PATH)
+    device = torch.cuda.get_device_name()
+    hit = tuning_cache.install(device, leaf, bucket, path) is not None
+    t = tuning_cache.autotune_cached(device, leaf, bucket, sample, stream, path)
+    return dict(t, source="tuning cache" if hit else "autotuned (then cached)")
+
+
 def timed_repeats(fn, min_s=10.0, max_reps=100000):
     """Runs fn until at least min_s seconds have passed (at most max_reps
     times); returns (repetitions, seconds)."""
@@ -317,6 +333,22 @@ def run_reference(a):
     return 0
 
 
+def add_executed(rooflines, work, leaf_ms, split_ms, peak_ops):
+    """Beside the full-model fraction (every trial counted as l or m
+    evaluations), the fraction over the evaluations the searches executed:
+    the two-phase leaf test skips the second part of most indices, and every
+    round of 32 indices is evaluated whole (counted on the device in the
+    work-counting build)."""
+    for name, key, ops, ms in (("leaf_search", "leaf_evals_executed", OPS_PER_LEAF_EVAL, leaf_ms),
+                               ("split_search", "split_evals_executed", OPS_PER_SPLIT_EVAL, split_ms)):
+        if name in rooflines and work.get(key) and ms > 0:
+            ach = work[key] * ops / (ms / 1e3) / 1e12
+            rooflines[name]["executed"] = {"evals": int(work[key]), "achieved": ach,
+                                           "frac": ach / rooflines[name]["peak"],
+                                           "evals_per_model_eval": work[key] / max(1, work[name.split("_")[0]
+                                                                                          + "_evals"])}
+
+
 def run_ours(a):
     import torch
 
@@ -346,7 +378,7 @@ def run_ours(a):
 
     # launch shapes of the searches for this leaf size, picked by the autotuner
     # on a seeded synthetic sample (untimed; results do not depend on them)
-    tuning = rs.recsplit_autotune(a.leaf, a.bucket, a.n, stream.cuda_stream)
+    tuning = tuned_shapes(rs, a.leaf, a.bucket, a.n, stream.cuda_stream)
     # timed steps record phase events only; the algorithmic work counts come
     # from one more build after the timed region (the searches are
     # deterministic, so every build of this input does the same work)
@@ -437,6 +469,7 @@ def run_ours(a):
     }
     for name, src in (("leaf_search", "search.cu"), ("split_search", "search.cu"), ("lookup", "lookup.cu")):
         rooflines[name]["ncu"] = counters_from_profiles(f"{name}_{tag}" if name != "lookup" else f"lookup_{tag}", src)
+    add_executed(rooflines, work, leaf_ms, split_ms, peak_ops)
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
         if r["traffic"] is not None:
@@ -473,17 +506,166 @@ def run_ours(a):
                 "phases_ms": {k: statistics.median(p[k] for p in profs)
                               for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")},
                 "work": {k: work[k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes",
-                                              "leaf_trials", "leaf_evals")},
+                                              "leaf_trials", "leaf_evals", "split_evals_executed",
+                                              "leaf_evals_executed")},
                 "bits_per_key": stats["bits_per_key"], "roofline": roofline, "rooflines": rooflines, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks}
         if a.serve_seconds > 0:
             line["serve"] = serve_run(rs, keys, a.serve_seconds, a.serve_rate, a.leaf, a.bucket)
+        if not a.no_extras:
+            del qdata, qoffs, qout
+            torch.cuda.empty_cache()
+            line["space_optimal"] = space_optimal_entry(rs, dev, stream)
+            torch.cuda.empty_cache()
+            line["batched"] = batched_entry(rs, dev, stream)
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a, keys)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def search_rooflines(prof, work, peak_ops):
+    peak_src = "152 SMs x 128 lanes/clk x 2070 MHz (issue-limited 32-bit integer instructions; derived)"
+    out = {}
+    for name, key, ops, ms_key in (("leaf_search", "leaf_evals", OPS_PER_LEAF_EVAL, "ms_leaf"),
+                                   ("split_search", "split_evals", OPS_PER_SPLIT_EVAL, "ms_split")):
+        ms = prof[ms_key]
+        ach = work[key] * ops / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        out[name] = {"bound": "alu", "ms": ms, "achieved": ach, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                     "ops_per_eval": ops, "peak_source": peak_src, "frac": ach / (peak_ops / 1e12)}
+    add_executed(out, work, prof["ms_leaf"], prof["ms_split"], peak_ops)
+    return out
+
+
+def space_optimal_entry(rs, dev, stream, steps=2, warmup=1, queries=10_000_000):
+    """The space-optimal configuration of Table 1: 10^6 64-bit keys (seed 2),
+    l = 16, b = 2000 (500 buckets; deep leaf searches of about 8.8e5 trials
+    per leaf).  Build keys/s over `steps` builds timed with CUDA events, the
+    phase times, the search rooflines (full-model and executed), and member
+    lookups/s."""
+    import torch
+    from paper_1910_06416_gb300 import inputs
+    n, leaf, b = 1_000_000, 16, 2000
+    keys = torch.from_numpy(inputs.u64_keys(n, 2).view(np.int64)).to(dev)
+    q = keys[torch.from_numpy(inputs.query_indices(n, queries, 2)).to(dev)]
+    out = torch.empty(queries, dtype=torch.int64, device=dev)
+    tuning = tuned_shapes(rs, leaf, b, n, stream.cuda_stream)
+    rs.recsplit_set_profiling(2)
+    sampler = ClockSampler(dev.index or 0)
+    bt, lt, profs = [], [], []
+    for step in range(warmup + steps):
+        if step == warmup:
+            sampler.start()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        h = rs.recsplit_build_u64(keys, leaf, b, stream.cuda_stream)
+        e1.record(stream)
+        rs.recsplit_lookup_u64(h, q, out, stream.cuda_stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if step >= warmup:
+            bt.append(e0.elapsed_time(e1))
+            lt.append(e1.elapsed_time(e2))
+            profs.append(rs.recsplit_last_profile())
+        stats = rs.recsplit_stats(h)
+        rs.recsplit_free(h)
+    clocks = sampler.stop()
+    rs.recsplit_set_profiling(1)
+    rs.recsplit_free(rs.recsplit_build_u64(keys, leaf, b, stream.cuda_stream))
+    work = rs.recsplit_last_profile()
+    rs.recsplit_set_profiling(0)
+    prof = {k: statistics.median(p[k] for p in profs)
+            for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")}
+    peak_ops = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    build_ms = statistics.median(bt)
+    return {"workload": f"{n} 64-bit keys (seed 2), l={leaf}, b={b}, {queries} member lookups",
+            "value": n / (build_ms / 1e3), "unit": "keys/s", "build_ms": build_ms, "steps": steps,
+            "lookup": {"value": queries / (statistics.median(lt) / 1e3), "unit": "queries/s"},
+            "phases_ms": prof, "bits_per_key": stats["bits_per_key"],
+            "work": {k: work[k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes", "leaf_trials",
+                                          "leaf_evals", "split_evals_executed", "leaf_evals_executed")},
+            "rooflines": search_rooflines(prof, work, peak_ops), "tuning": tuning, "clocks": clocks}
+
+
+def batched_entry(rs, dev, stream, steps=2, warmup=1):
+    """The batched configuration: 4096 independent structures (sizes
+    log-uniform in [10^3, 10^6), seed 3; leaf sizes {5, 8, 12} x bucket sizes
+    {5, 100, 2000}) built in one batched pass (timed with CUDA events), against
+    one build per launch of the same sets, then 10^9 batched lookups."""
+    import torch
+    from paper_1910_06416_gb300 import inputs
+    plan = inputs.batch_sets(4096, 1000, 1000000, 3)
+    keys = [inputs.device_splitmix64(sd, n, device=dev) for n, _, _, sd in plan]
+    total = sum(p[0] for p in plan)
+    tunings = {}
+    for leaf in sorted({p[1] for p in plan}):
+        b = max((p for p in plan if p[1] == leaf), key=lambda p: p[0])[2]
+        tunings[leaf] = tuned_shapes(rs, leaf, b, 1 << 20, stream.cuda_stream)
+    sets = [(k, l, b) for k, (n, l, b, _) in zip(keys, plan)]
+    sampler = ClockSampler(dev.index or 0)
+    bt, handles, bits = [], None, 0
+    for step in range(warmup + steps):
+        if step == warmup:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs = rs.recsplit_build_batch(sets, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if step >= warmup:
+            bt.append(e0.elapsed_time(e1))
+        if step == warmup + steps - 1:
+            handles = hs
+            bits = sum(rs.recsplit_stats(h)["total_bits"] for h in hs)
+        else:
+            for h in hs:
+                rs.recsplit_free(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    single_bits = 0
+    for k, l, b in sets:
+        h = rs.recsplit_build_u64(k, l, b, stream.cuda_stream)
+        single_bits += rs.recsplit_stats(h)["total_bits"]
+        rs.recsplit_free(h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1)
+    q, chunk = 1_000_000_000, 100_000_000
+    sizes = torch.tensor([p[0] for p in plan], device=dev, dtype=torch.int64)
+    flat = torch.cat(keys)
+    del keys
+    offs = torch.zeros(len(plan) + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(sizes, 0, out=offs[1:])
+    out = torch.empty(chunk, dtype=torch.int64, device=dev)
+    look_ms = 0.0
+    for c0 in range(0, q, chunk):
+        r = inputs.device_splitmix64(0xC4C4, 2 * chunk, start=2 * c0, device=dev)
+        ids = ((r[0::2] >> 1) % len(plan)).to(torch.int32)
+        qk = flat[offs[ids.long()] + (r[1::2] >> 1) % sizes[ids.long()]]
+        del r
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs.recsplit_lookup_batch(handles, ids, qk, out, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        look_ms += e0.elapsed_time(e1)
+        del ids, qk
+    clocks = sampler.stop()
+    for h in handles:
+        rs.recsplit_free(h)
+    del flat, out
+    batch_ms = statistics.median(bt)
+    return {"workload": "4096 sets of 64-bit keys, sizes log-uniform in [1e3, 1e6) (seed 3), "
+                        "l in {5, 8, 12} x b in {5, 100, 2000}, 1e9 batched lookups",
+            "sets": len(plan), "keys": total, "value": total / (batch_ms / 1e3), "unit": "keys/s",
+            "batch_ms": batch_ms, "steps": steps,
+            "one_per_launch": {"value": total / (single_ms / 1e3), "unit": "keys/s", "ms": single_ms},
+            "speedup_vs_one_per_launch": single_ms / batch_ms,
+            "bits_per_key": bits / total, "bits_per_key_one_per_launch": single_bits / total,
+            "lookup": {"value": q / (look_ms / 1e3), "unit": "queries/s", "queries": q},
+            "tuning": {str(k): v for k, v in tunings.items()}, "clocks": clocks}
 
 
 def run_u64(a):
@@ -624,35 +806,109 @@ def run_batch(a):
     return 0
 
 
+def model_tree_bits_per_key(rs, leaf, bucket):
+    """Expected Golomb-Rice bits per key of the splitting trees (Sec. 5.4):
+    a node whose trials succeed with probability p and whose parameter is r
+    costs r + 1 / (1 - (1 - p)^(2^r)) bits; p is m!/m^m for a leaf and that
+    times k^k/k! per part for a split (Sec. 5.1, 5.2); bucket sizes are
+    Poisson(b)."""
+    import math
+    s_aggr = max(2, -(-(7 * leaf + 10) // 20))
+    t_aggr = -(-(21 * leaf + 90) // 100) if leaf >= 7 else 2
+    lower, upper = s_aggr * leaf, s_aggr * t_aggr * leaf
+    m_hi = int(bucket + 8 * math.sqrt(bucket) + 16)
+    r = rs.recsplit_golomb_rice_params(leaf, m_hi)
+
+    def parts(m):
+        if m <= leaf:
+            return []
+        if m > upper:
+            left = -(-(m // 2) // upper) * upper
+            return [left, m - left]
+        unit = leaf if m <= lower else lower
+        f = -(-m // unit)
+        return [unit] * (f - 1) + [m - unit * (f - 1)]
+
+    memo = {0: 0.0, 1: 0.0}
+
+    def bits(m):
+        if m in memo:
+            return memo[m]
+        ps = parts(m)
+        logp = math.lgamma(m + 1) - m * math.log(m)
+        for k in ps:
+            logp += k * math.log(k) - math.lgamma(k + 1)
+        p = math.exp(logp)
+        rr = int(r[m])
+        v = rr + 1.0 / (-math.expm1((2 ** rr) * math.log1p(-p))) + sum(bits(k) for k in ps)
+        memo[m] = v
+        return v
+
+    total, w = 0.0, 0.0
+    for m in range(0, m_hi + 1):
+        pm = math.exp(m * math.log(bucket) - bucket - math.lgamma(m + 1)) if m else math.exp(-bucket)
+        total += pm * bits(m)
+        w += pm
+    return total / w / bucket
+
+
 def run_sweep(a):
-    """Space and construction time over leaf sizes 2..18 and bucket sizes
-    {5, 100, 2000} (64-bit keys, seed 4): the data of the paper's space
-    figure and its construction-time trend (about e per unit of leaf size)."""
+    """Space and construction time over leaf sizes 2..21 and bucket sizes
+    {5, 100, 2000} (64-bit keys, seed 4; fewer keys as the leaf searches grow,
+    the sizes of the stored oracle digests): the data of the paper's space
+    figure and of its construction-time trend (about e per unit of leaf size,
+    Sec. 8).  Each point's structure is compared with the oracle's stored
+    digest, its bits/key with the Sec. 5.4 model."""
+    import hashlib
     import torch
 
     from paper_1910_06416_gb300 import build as lib_build, inputs
     import paper_1910_06416_gb300.recsplit as rs
 
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import digest_cases as D
+    stored = {(p["leaf"], p["bucket"], p["n"]): p["sha256"] for p in (D.load("oracle_digests_sweep.json") or {})
+              .get("points", [])}
     lib_build.build()
     rs.lib()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    rs.recsplit_set_profiling(True)
     rows = []
-    for leaf in range(2, 19):
-        n = 1_000_000 if leaf <= 14 else (200_000 if leaf <= 16 else 20_000)
-        keys = torch.from_numpy(inputs.u64_keys(n, 4).view(np.int64)).to(dev)
-        for b in (5, 100, 2000):
-            ts = []
-            for rep in range(2):
-                h = rs.recsplit_build_u64(keys, leaf, b, stream.cuda_stream)
-                ts.append(rs.recsplit_last_profile()["ms_total"])
-                st = rs.recsplit_stats(h)
+    keys = {}
+    for leaf, b, n in D.sweep_points():
+        if n not in keys:
+            keys.clear()
+            keys[n] = torch.from_numpy(inputs.u64_keys(n, D.SWEEP_SEED).view(np.int64)).to(dev)
+        ts = []
+        rs.recsplit_set_profiling(2)
+        for rep in range(3):
+            h = rs.recsplit_build_u64(keys[n], leaf, b, stream.cuda_stream)
+            ts.append(rs.recsplit_last_profile()["ms_total"])
+            if rep < 2:
                 rs.recsplit_free(h)
-            rows.append({"leaf": leaf, "bucket": b, "n": n, "bits_per_key": st["bits_per_key"],
-                         "tree_bits_per_key": st["tree_bits_per_key"], "build_ms": min(ts),
-                         "keys_per_s": n / (min(ts) / 1e3)})
+        st = rs.recsplit_stats(h)
+        digest = hashlib.sha256(np.ascontiguousarray(rs.recsplit_serialize(h), dtype="<u8").tobytes()).hexdigest()
+        rs.recsplit_free(h)
+        rs.recsplit_set_profiling(1)
+        rs.recsplit_free(rs.recsplit_build_u64(keys[n], leaf, b, stream.cuda_stream))
+        work = rs.recsplit_last_profile()
+        rs.recsplit_set_profiling(0)
+        want = stored.get((leaf, b, n))
+        ms = min(ts[1:])
+        rows.append({"leaf": leaf, "bucket": b, "n": n, "bits_per_key": st["bits_per_key"],
+                     "tree_bits_per_key": st["tree_bits_per_key"],
+                     "model_tree_bits_per_key": model_tree_bits_per_key(rs, leaf, b),
+                     "build_ms": ms, "keys_per_s": n / (ms / 1e3),
+                     "evals_per_key": (work["leaf_evals"] + work["split_evals"]) / n,
+                     "oracle_digest": None if want is None else digest == want})
+    for row in rows:
+        prev = next((r for r in rows if r["leaf"] == row["leaf"] - 1 and r["bucket"] == row["bucket"]), None)
+        if prev:
+            row["time_per_key_ratio_to_prev_leaf"] = (row["build_ms"] / row["n"]) / (prev["build_ms"] / prev["n"])
+            row["evals_per_key_ratio_to_prev_leaf"] = row["evals_per_key"] / max(prev["evals_per_key"], 1e-30)
+    checked = [r["oracle_digest"] for r in rows if r["oracle_digest"] is not None]
     print(json.dumps({"metric": "space and construction time over (leaf, bucket)", "workload": "sweep",
+                      "points": len(rows), "oracle_identical": sum(checked), "oracle_checked": len(checked),
                       "rows": rows}), flush=True)
     return 0
 

@@ -128,8 +128,10 @@ typedef struct recsplit_keyset {
 } recsplit_keyset_t;
 
 /* Builds count independent structures in one pass (Sec. 4 applied to every
- * set; buckets of all sets are searched together, the search phase runs as
- * one CUDA graph of persistent kernels).  outs[i] receives the structure of
+ * set; buckets of all sets are searched together: one persistent kernel per
+ * tree level and per leaf size covers every set, and the search phase is
+ * captured into one CUDA graph per call and launched as one).  outs[i]
+ * receives the structure of
  * sets[i], identical to what recsplit_build_u64 / _bytes would build from it.
  * All key arrays must be device memory; at most 2^32 - 1 keys in total and
  * at most 25 distinct leaf sizes.  The structures share one device arena,
@@ -205,12 +207,17 @@ typedef struct recsplit_profile {
   uint64_t leaf_evals;
   uint32_t launches;      /* kernels launched by the build                      */
   uint32_t split_levels;  /* launches of the split search (one per tree level)  */
+  uint64_t leaf_evals_executed;   /* hash evaluations the leaf searches executed: the
+                                     two-phase test skips the second part of most
+                                     indices, and every round is evaluated whole     */
+  uint64_t split_evals_executed;  /* the same for the split searches                 */
 } recsplit_profile_t;
 
 /* Per-build profiling for the calling host thread: 0 off; 1 phase events
  * and the algorithmic work counts (two small kernels after the build's last
- * phase); 2 phase events only (the work fields of the profile are 0).  Other
- * values fail with RECSPLIT_E_INVALID. */
+ * phase, and counters the searches update per round); 2 phase events only
+ * (the work fields of the profile are 0).  Other values fail with
+ * RECSPLIT_E_INVALID. */
 int recsplit_set_profiling(int enabled);
 
 /* Profile of the last successful build on the calling host thread. */
@@ -221,11 +228,14 @@ uint64_t recsplit_launch_count(void);
 
 /* ---------------------------------------------------------------------
  * Serving engine: a request loop that builds and queries structures as
- * requests arrive, keeping the structures resident in device memory.  Builds
- * waiting while others run are admitted in arrival order as the memory budget
- * allows and built together in one multi-set build; lookups waiting are served
- * together in one batched launch on a stream of their own, overlapping the
- * builds.  Every result equals that of the same request served alone.
+ * requests arrive, keeping the structures resident in device memory.  Waiting
+ * builds are admitted in arrival order as the memory budget allows, by
+ * whichever of the build workers is free, and the builds one worker admits
+ * together run as one multi-set build; rounds of several workers run at once,
+ * short rounds on streams of higher priority than long ones.  Lookups waiting
+ * are served together in one batched launch on a stream of the highest
+ * priority, overlapping the builds.  Every result equals that of the same
+ * request served alone.
  * Buffers passed to submit calls are host memory (the engine copies inputs
  * to the device when it starts the request) and must stay valid (inputs
  * unchanged, outputs untouched) until the request completes.
@@ -237,6 +247,7 @@ typedef struct recsplit_server_config {
   uint64_t hbm_budget_bytes;  /* device bytes for resident structures + builds in flight (0: 64 GiB) */
   uint32_t max_build_batch;   /* builds per device round (0: 64)                               */
   uint64_t max_lookup_batch;  /* queries per lookup launch (0: 2^26)                            */
+  uint32_t build_workers;     /* build rounds that may run at once (0: 3; at most 16)          */
 } recsplit_server_config_t;
 
 typedef struct recsplit_completion {

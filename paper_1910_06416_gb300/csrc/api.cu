@@ -512,6 +512,7 @@ int recsplit_deserialize(const void* buf, size_t len, void* stream, recsplit_t**
   }
   h->d_blob = static_cast<uint64_t*>(h->blob_mem->p);
   h->d_table = static_cast<uint64_t*>(h->table_mem->p);
+  h->table_mmax = T.mmax;
   if (cudaMemcpyAsync(h->d_blob, buf, len, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(h->d_table, T.device_words.data(), T.device_words.size() * sizeof(uint64_t),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -709,6 +709,13 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     return rc;
   RS_CUDA(cudaMemsetAsync(counters, 0, (3 + 2 * kMaxClasses) * sizeof(uint32_t), s));
   RS_CUDA(cudaMemsetAsync(d_error, 0, sizeof(int), s));
+  // work counting: the searches also count the evaluations they execute
+  const bool count_work = timer.on && work_counting_enabled();
+  unsigned long long* exec = nullptr;
+  if (count_work) {
+    if ((rc = sc.alloc(&exec, 2))) return rc;
+    RS_CUDA(cudaMemsetAsync(exec, 0, 2 * sizeof(unsigned long long), s));
+  }
   RS_CUDA(cudaMemsetAsync(sizes, 0, (K + 1) * sizeof(uint32_t), s));
   SearchArgs a{};
   a.keys[0] = keys[0];
@@ -735,6 +742,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   a.full_n = counters + 3;
   a.part_n = counters + 3 + kMaxClasses;
   a.error = d_error;
+  a.exec_count = exec;
   a.split_in = q_split[0];
   a.split_in_count = counters + 0;
   if (NB) {
@@ -750,6 +758,38 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   for (uint32_t c = 0; c < nclass; c++) {
     level_max[c] = h_cls_max[c];
     max_leaf = std::max(max_leaf, class_leaf[c]);
+  }
+
+  // Level plan: the largest node of every split level, and whether the
+  // level's nodes are heavy enough to be searched shared (a node's expected
+  // trials x keys of at least 2^21 evaluations: a level of such nodes ends
+  // on a few long geometric searches)
+  std::vector<uint64_t> plan_mx;
+  std::vector<char> plan_share;
+  {
+    std::vector<uint64_t> lm = level_max;
+    for (;;) {
+      uint64_t mx = 0;
+      double heavy = 0;
+      for (uint32_t c = 0; c < nclass; c++)
+        if (lm[c] > class_leaf[c]) {
+          mx = std::max(mx, lm[c]);
+          heavy = std::max(heavy, double(T[c].expected_trials[lm[c]]) * double(lm[c]));
+        }
+      if (mx == 0 || plan_mx.size() > kMaxDepth + 1) break;
+      plan_mx.push_back(mx);
+      plan_share.push_back(heavy >= double(1 << 21));
+      for (uint32_t c = 0; c < nclass; c++)
+        lm[c] = lm[c] > class_leaf[c] ? next_level_max(make_strategy(class_leaf[c]), lm[c]) : 0;
+    }
+  }
+  SharedNodes shared{};
+  if (std::find(plan_share.begin(), plan_share.end(), 1) != plan_share.end()) {
+    if ((rc = sc.alloc(&shared.best, split_cap)) || (rc = sc.alloc(&shared.next, split_cap)) ||
+        (rc = sc.alloc(&shared.refs, split_cap)) || (rc = sc.alloc(&shared.cap, split_cap)) ||
+        (rc = sc.alloc(&shared.flag, split_cap)) ||
+        (rc = sc.alloc(&shared.owned, kSharedCtas)))
+      return rc;
   }
 
   // A3 (split levels), A4 (leaves), A5 (lengths): optionally one CUDA graph
@@ -787,7 +827,12 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
       a.split_out = q_split[cur ^ 1];
       a.split_out_count = counters + (cur ^ 1);
       RS_CUDA(cudaMemsetAsync(a.split_out_count, 0, sizeof(uint32_t), ws));
-      int r = launch_split_level(a, mx, max_leaf, sm_count, ws);
+      const bool share = size_t(level) < plan_share.size() && plan_share[level];
+      if (share) {
+        RS_CUDA(cudaMemsetAsync(shared.flag, 0, split_cap * sizeof(unsigned int), ws));
+        RS_CUDA(cudaMemsetAsync(shared.owned, 0xFF, kSharedCtas * sizeof(unsigned int), ws));
+      }
+      int r = launch_split_level(a, mx, max_leaf, sm_count, ws, share ? &shared : nullptr);
       if (r) return r;
       for (uint32_t c = 0; c < nclass; c++)
         level_max[c] = level_max[c] > class_leaf[c] ? next_level_max(make_strategy(class_leaf[c]), level_max[c]) : 0;
@@ -934,7 +979,6 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
   count_launch();
   timer.mark();
   unsigned long long* work = nullptr;
-  const bool count_work = timer.on && work_counting_enabled();
   if (count_work) {
     uint32_t* code_leaf;
     if ((rc = sc.alloc(&work, 6)) || (rc = sc.alloc(&code_leaf, K + 1))) return rc;
@@ -947,8 +991,11 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     }
   }
   RS_CUDA(cudaGetLastError());
-  unsigned long long w[6] = {0, 0, 0, 0, 0, 0};
-  if (count_work) RS_CUDA(cudaMemcpyAsync(w, work, sizeof(w), cudaMemcpyDeviceToHost, s));
+  unsigned long long w[6] = {0, 0, 0, 0, 0, 0}, x[2] = {0, 0};
+  if (count_work) {
+    RS_CUDA(cudaMemcpyAsync(w, work, sizeof(w), cudaMemcpyDeviceToHost, s));
+    RS_CUDA(cudaMemcpyAsync(x, exec, sizeof(x), cudaMemcpyDeviceToHost, s));
+  }
   RS_CUDA(cudaStreamSynchronize(s));
 
   for (uint32_t i = 0; i < count; i++) {
@@ -959,6 +1006,7 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     h->table_mem = table_mem;
     h->d_blob = d_arena + blob_off[i];
     h->d_table = const_cast<uint64_t*>(ct.t[hs[i].cls]);
+    h->table_mmax = ct.mmax[hs[i].cls];
     h->ncodes = h->header[H_CODES];
     h->range_size = h_R[i];
     h->device = dev;
@@ -978,6 +1026,8 @@ int build_sets(const SetInput* in, uint32_t count, const BuildOptions& opt, cuda
     pr.leaf_nodes = w[3];
     pr.leaf_trials = w[4];
     pr.leaf_evals = w[5];
+    pr.leaf_evals_executed = x[0];
+    pr.split_evals_executed = x[1];
     pr.launches = launches_since(launch0);
     pr.split_levels = split_levels;
     store_profile(pr);

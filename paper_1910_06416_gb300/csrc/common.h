@@ -79,7 +79,23 @@ struct Tables {
 // Device words per node size m: w0 = subtree fixed bits | subtree codes << 32;
 // w1 = unit | fanout << 32 | r << 40; w2 = expected trials;
 // w3 = ceil(2^32 / unit) | subtree output range << 32.
+// After the kTableWords * (mmax + 1) words come the lookup records, one
+// 16-byte LookupRecord per node size 0 .. mmax (lookup_records()).
 int build_tables(uint32_t leaf, uint32_t extra, uint64_t mmax, Tables* out, std::string* err);
+
+// What the descent of a lookup needs at a node of m keys, in one 16-byte
+// load: unit = size of every child but the last (0 at a leaf); magic =
+// ceil(2^32 / unit) when floor(v * magic / 2^32) = floor(v / unit) for every
+// v < m, else 0 (divide); fixed = fixed bits of a subtree of `unit` keys;
+// info = codes of a subtree of `unit` keys (bits 0..22) | r(m) << 23 |
+// fanout << 28 (0 at a leaf).
+struct LookupRecord {
+  uint32_t unit, magic, fixed, info;
+};
+constexpr int kLookupCodeBits = 23;
+inline const LookupRecord* lookup_records(const uint64_t* table, uint64_t table_mmax) {
+  return reinterpret_cast<const LookupRecord*>(table + kTableWords * (table_mmax + 1));
+}
 
 // Host-side check of a serialized structure (validate.cpp): the lists and
 // their inventories (s, o: decoded prefix sums of the bucket output ranges
@@ -103,7 +119,8 @@ struct Handle {
   Layout layout;
   std::shared_ptr<DeviceMem> blob_mem, table_mem;
   uint64_t* d_blob = nullptr;   // serialized structure, device resident
-  uint64_t* d_table = nullptr;  // device tables (kTableWords per node size)
+  uint64_t* d_table = nullptr;  // device tables (kTableWords per node size, then the lookup records)
+  uint64_t table_mmax = 0;      // largest node size the tables cover
   uint64_t ncodes = 0;
   int device = 0;
 };
@@ -117,6 +134,7 @@ struct View {
   const uint64_t* anchors;
   const uint16_t* subs;
   const uint64_t* table;  // kTableWords words per size
+  const LookupRecord* rec;  // one lookup record per size
   const uint64_t* so;  // s_i, o_i of every bucket decoded beforehand, or null
   uint64_t tree_words32;  // 32-bit words of the tree section (code scans stop there)
   uint64_t mmax;       // largest bucket (the tables cover sizes 0 .. mmax)
@@ -241,9 +259,29 @@ struct SearchArgs {
   // queue capacities: an append beyond one sets RECSPLIT_E_INVALID in *error
   // instead of writing (the sizes are computed to suffice; this guards them)
   uint32_t split_cap, full_cap[kMaxClasses], part_cap[kMaxClasses];
+  // work counting (null unless counting): [0] hash evaluations the leaf
+  // searches executed, [1] those of the split searches
+  unsigned long long* exec_count;
 };
 
-int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s);
+// State of the nodes of one split level for the shared search (search.cu):
+// per node its best index so far, block counter, participants, most
+// participants and state (0 none, 1 open, 2 closed; zeroed per level), and
+// per CTA the node it owns (~0 when none; set to ~0 per level).  kSharedCtas bounds the grid.
+struct SharedNodes {
+  uint64_t* best;
+  unsigned int* next;
+  unsigned int* refs;
+  unsigned int* cap;  // most participants a node takes
+  unsigned int* flag;
+  unsigned int* owned;
+};
+constexpr uint32_t kSharedCtas = 4096;
+
+// share: null for the one-group-per-node search; else the level is searched
+// with nodes shared by the CTAs that find the queue empty (st zeroed as above)
+int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s,
+                       const SharedNodes* share = nullptr);
 int launch_leaves(const SearchArgs& a, uint32_t leaf, uint32_t extra, int sm_count, cudaStream_t s);
 
 // Launch shapes of the searches for one leaf size (see recsplit_tuning_t).

@@ -29,10 +29,16 @@ __device__ __forceinline__ uint64_t ef_offset(const View& v, uint64_t b, uint64_
   return static_cast<uint64_t>(z + static_cast<int64_t>(bs));
 }
 
-// RANGE: the structure has a leaf range extra (perfect, non-minimal
-// variant); false compiles the minimal structure's path alone.
+// Descent of a bucket of m >= 2 keys whose code starts at bit o: the minimal
+// structure's path (descend_min) and the path of the perfect, non-minimal
+// variant with its output ranges (descend_range).  RANGE: the structure has a
+// leaf range extra; false compiles the minimal structure's path alone.
+__device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
+__device__ __forceinline__ uint64_t descend_range(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
 template <bool RANGE>
-__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
+__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
+  return RANGE ? descend_range(v, s0, m, o, lo) : descend_min(v, s0, m, o, lo);
+}
 
 // Output range of a subtree of m keys (table word 3, upper half).
 __device__ __forceinline__ uint64_t node_range(const View& v, uint64_t m) {
@@ -142,11 +148,101 @@ __device__ __forceinline__ uint32_t code_select(const uint32_t* __restrict__ t, 
   return (w << 5) + select_in_word32(word, rank);
 }
 
-// Sec. 4 / 6.2: descent of the splitting tree of a bucket of m keys whose
-// code starts at bit o.
-template <bool RANGE>
-__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
-  const uint32_t extra = RANGE ? v.extra : 0;
+// Position of the set bit of rank k (0-based) in a 64-bit word (k < popc).
+__device__ __forceinline__ uint32_t select_in_word64(uint64_t x, uint32_t k) {
+  const uint32_t lo = static_cast<uint32_t>(x);
+  const uint32_t c = __popc(lo);
+  const bool up = k >= c;
+  return (up ? 32u : 0u) + select_in_word32(up ? static_cast<uint32_t>(x >> 32) : lo, up ? k - c : k);
+}
+
+// (i * 64 + d) * W = i * (64 W) + d * W: the family key of index i at depth d
+// as one multiply-add, the depth term advancing by W per level.
+constexpr uint64_t kWeyl64 = kWeyl << 6;
+
+// Sec. 4 / 6.2: descent of the splitting tree of a bucket of m >= 2 keys
+// whose code starts at bit o, for the minimal structure.  Per node of m keys
+// one 16-byte lookup record gives r, the fanout, the part size, the
+// reciprocal for the part index, and the fixed bits and codes of a part-sized
+// subtree (to skip the earlier siblings).  The unary part of the bucket's
+// code (one code per node, about 1.5 bits each) is held in a 64-bit register
+// window from its first bit, so reading a unary code is a find-first-set and
+// skipping j * codes(unit) codes a select inside the window; a unary part that
+// runs past the window continues with scans of the code words.  Fixed parts
+// are read with two loads and a funnel shift, without a branch.
+__device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
+  const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
+  const uint64_t left = v.tree_words32 - (o >> 5);
+  const uint32_t end = left < 0xFFFFFFFFull ? static_cast<uint32_t>(left) : 0xFFFFFFFFu;
+  uint32_t fixed = static_cast<uint32_t>(o & 31);
+  // the unary part starts after the fixed parts of all the bucket's codes
+  const uint32_t u0 = fixed + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
+  uint64_t win;
+  {
+    const uint32_t uw = u0 >> 5, us = u0 & 31;
+    const uint32_t a0 = __ldg(t + uw);
+    const uint32_t a1 = uw + 1 < end ? __ldg(t + uw + 1) : 0u;
+    const uint32_t a2 = uw + 2 < end ? __ldg(t + uw + 2) : 0u;
+    win = (uint64_t(__funnelshift_r(a1, a2, us)) << 32) | __funnelshift_r(a0, a1, us);
+  }
+  uint32_t up = 0;  // bit of the next unary code, relative to u0
+  const uint64_t xpre = pre_key(lo);
+  uint64_t dkey = 0;  // depth * W
+  uint32_t c = 0;     // keys of the siblings left behind
+  const uint4* __restrict__ rec = reinterpret_cast<const uint4*>(v.rec);
+  uint4 nd = __ldg(rec + m);
+  for (;;) {
+    const uint32_t r = (nd.w >> kLookupCodeBits) & 31, fanout = nd.w >> 28;
+    const uint32_t fw = fixed >> 5;
+    const uint32_t f0 = __ldg(t + fw);
+    const uint32_t f1 = fw + 1 < end ? __ldg(t + fw + 1) : 0u;
+    const uint32_t low = __funnelshift_r(f0, f1, fixed & 31) & ((1u << r) - 1u);
+    fixed += r;
+    const uint64_t rest = up < 64 ? win >> up : 0ull;
+    uint32_t one;  // the unary code's one bit, relative to u0
+    if (rest) {
+      one = up + static_cast<uint32_t>(__ffsll(static_cast<long long>(rest)) - 1);
+    } else {
+      const uint32_t a = code_next_one(t, u0 + up, end);
+      if (a == ~0u) return ~0ull;
+      one = a - u0;
+    }
+    const uint64_t seed = (uint64_t(one - up) << r) | low;
+    up = one + 1;
+    const uint64_t k = seed * kWeyl64 + dkey;
+    const uint32_t val = __umulhi(family_top32(xpre, k ^ (k >> 30)), m);
+    if (fanout == 0) return s0 + c + val;
+    const uint32_t part = min(nd.y ? __umulhi(val, nd.y) : val / nd.x, fanout - 1);
+    if (part) {
+      fixed += part * nd.z;
+      // skip the unary codes of the part earlier siblings (none when a
+      // part-sized subtree has no code, e.g. single keys): up moves past the
+      // one of rank part * codes(unit) - 1
+      const uint32_t skip = part * (nd.w & ((1u << kLookupCodeBits) - 1));
+      if (skip) {
+        const uint64_t x = up < 64 ? win & (~0ull << up) : 0ull;
+        if (static_cast<uint32_t>(__popcll(x)) >= skip) {
+          up = select_in_word64(x, skip - 1) + 1;
+        } else {
+          const uint32_t a = code_select(t, u0 + up, skip - 1, end);
+          if (a == ~0u) return ~0ull;
+          up = a - u0 + 1;
+        }
+      }
+      c += part * nd.x;
+    }
+    m = part + 1 < fanout ? nd.x : m - nd.x * (fanout - 1);
+    if (m <= 1) return s0 + c;
+    nd = __ldg(rec + m);
+    dkey += kWeyl;
+  }
+}
+
+// The same descent for structures with a leaf range extra (perfect,
+// non-minimal variant): leaves map into m + e values, and the siblings left
+// behind contribute their output ranges.
+__device__ __forceinline__ uint64_t descend_range(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
+  const uint32_t extra = v.extra;
   const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
   const uint64_t left = v.tree_words32 - (o >> 5);
   const uint32_t end = left < 0xFFFFFFFFull ? static_cast<uint32_t>(left) : 0xFFFFFFFFu;
@@ -382,6 +478,7 @@ View make_view(const Handle& h) {
   v.anchors = h.d_blob + h.layout.anchors;
   v.subs = reinterpret_cast<const uint16_t*>(h.d_blob + h.layout.subs);
   v.table = h.d_table;
+  v.rec = lookup_records(h.d_table, h.table_mmax);
   v.tree_words32 = 2 * words_of_bits(H[H_TBITS]);
   v.nb = H[H_NB];
   v.beta = H[H_BETA];

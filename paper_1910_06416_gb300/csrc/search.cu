@@ -171,7 +171,7 @@ template <int MODE>
 __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ keys, const SplitParams& sp,
                                                   uint32_t depth, uint32_t wig, uint32_t gwarps, uint32_t lane,
                                                   uint64_t* best, uint64_t stall, uint64_t limit,
-                                                  int* err) {
+                                                  int* err, unsigned long long* exec) {
   bool checked = false;
   uint32_t rounds = 0;
   for (uint64_t base = uint64_t(wig) * 32;; base += uint64_t(gwarps) * 32) {
@@ -199,6 +199,7 @@ __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ k
     bool ok = split_trial<MODE>(keys, sp, kp);
     if ((MODE == 5 || (MODE == 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
     const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+    if (exec && lane == 0) *exec += 32 * sp.m;
     if (hits) {
       if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(best), base + __ffs(hits) - 1);
       break;
@@ -208,16 +209,17 @@ __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ k
 
 __device__ __forceinline__ void split_search(const uint64_t* __restrict__ keys, const SplitParams& sp, int mode,
                                              uint32_t depth, uint32_t wig, uint32_t gwarps, uint32_t lane,
-                                             uint64_t* best, uint64_t stall, uint64_t limit, int* err) {
+                                             uint64_t* best, uint64_t stall, uint64_t limit, int* err,
+                                             unsigned long long* exec) {
   switch (mode) {
-    case 0: split_search_warp<0>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    case 1: split_search_warp<1>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    case 3: split_search_warp<3>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    case 4: split_search_warp<4>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    case 5: split_search_warp<5>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    case 6: split_search_warp<6>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    case 7: split_search_warp<7>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
-    default: split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err); break;
+    case 0: split_search_warp<0>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
+    case 1: split_search_warp<1>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
+    case 3: split_search_warp<3>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
+    case 4: split_search_warp<4>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
+    case 5: split_search_warp<5>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
+    case 6: split_search_warp<6>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
+    case 7: split_search_warp<7>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
+    default: split_search_warp<2>(keys, sp, depth, wig, gwarps, lane, best, stall, limit, err, exec); break;
   }
 }
 
@@ -258,12 +260,100 @@ __device__ void emit_children(const SearchArgs& a, const Node& nd, const uint64_
   }
 }
 
+// Search parameters of a split node; returns the count mode (split_trial).
+__device__ __forceinline__ int split_setup(const Node& nd, const uint64_t* table, SplitParams& sp) {
+  const uint64_t w1 = table[kTableWords * nd.m + 1];
+  sp.m = nd.m;
+  sp.unit = static_cast<uint32_t>(w1);
+  sp.fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
+  sp.bits = 32 - __clz(nd.m);
+  sp.magic = static_cast<uint32_t>((0x100000000ull + sp.unit - 1) / sp.unit);
+  const uint32_t fields = sp.fanout - 1;
+  sp.target = 0;
+  for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
+  sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
+  // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
+  int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+  if (sp.fanout == 4 && nd.m == 4 * sp.unit && nd.m < 256) {
+    mode = 6;
+    sp.cum_target = sp.unit | (sp.unit << 8) | (sp.unit << 16);
+  } else if (sp.fanout >= 5 && nd.m == sp.fanout * sp.unit && sp.unit >= 2 && nd.m < 65536) {
+    const uint32_t nb = nd.m < 256 && fields * 8 <= 32 ? 8 : 32 - __clz(sp.unit);
+    if (fields * nb <= 32) {
+      mode = 7;
+      sp.confirm = (1u << nb) <= nd.m;
+      sp.nbits = nb;
+      sp.nmask = fields * nb == 32 ? ~0u : (1u << (fields * nb)) - 1;
+      sp.ntarget = 0;
+      for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * nb);
+    }
+  }
+  if (mode == 1 && sp.fanout * sp.unit != nd.m) {
+    sp.nbits = 32 - __clz(sp.unit);
+    if (fields * sp.nbits <= 32) {
+      mode = 5;
+      sp.nmask = fields * sp.nbits == 32 ? ~0u : (1u << (fields * sp.nbits)) - 1;
+      sp.ntarget = 0;
+      for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * sp.nbits);
+    }
+  }
+  if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= kMaxThresholdFanout && fields * sp.bits <= 32) {
+    mode = 1 + static_cast<int>(sp.fanout);
+    // T_k = ceil(k * unit * 2^32 / m); field k - 1 must count k * unit keys
+    sp.thr1 = static_cast<uint32_t>(((uint64_t(sp.unit) << 32) + nd.m - 1) / nd.m);
+    sp.thr2 = static_cast<uint32_t>(((uint64_t(2 * sp.unit) << 32) + nd.m - 1) / nd.m);
+    sp.cum_target = sp.unit + (fields >= 2 ? (2 * sp.unit) << sp.bits : 0u);
+    sp.inc1 = 1u << sp.bits;
+  }
+  return mode;
+}
+
+// Stores the node's index and partitions its keys with it into the
+// children's ranges of the other key array, then queues the children (the
+// threads tig < gthreads of one group; `fill` is the group's 16 part cursors,
+// zero on entry; `mine` the node's keys if staged, else null).
+__device__ __forceinline__ void partition_node(const SearchArgs& a, const Node& nd, uint64_t seed,
+                                               const uint64_t* mine, uint32_t tig, uint32_t gthreads, uint32_t lane,
+                                               bool first_warp, uint32_t* fill) {
+  const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
+  const uint64_t* table = a.table[cls];
+  const uint64_t w1 = table[kTableWords * nd.m + 1];
+  const uint32_t unit = static_cast<uint32_t>(w1), fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
+  const bool divide = nd.m >= 65536 || unit < 2;
+  const uint32_t magic = divide ? 0u : static_cast<uint32_t>((0x100000000ull + unit - 1) / unit);
+  const uint64_t* src = a.keys[depth & 1] + nd.start;
+  uint64_t* dst = a.keys[(depth + 1) & 1] + nd.start;
+  if (tig == 0) {
+    a.seeds[nd.slot] = seed;
+    a.sizes[nd.slot] = nd.m;
+  }
+  const uint64_t kp = family_key(seed, depth);
+  const uint64_t* from = mine ? mine : src;
+  for (uint32_t j = tig; j < nd.m; j += gthreads) {
+    const uint64_t x = from[j];
+    const uint32_t v = phi_pre(x, kp, nd.m);
+    const uint32_t part = min(divide ? v / unit : __umulhi(v, magic), fanout - 1);
+    const uint32_t pos = atomicAdd(&fill[part], 1u);
+    const uint32_t at = part * unit + pos;
+    if (at < nd.m)
+      dst[at] = x;
+    else
+      set_error(a.error, RECSPLIT_E_INVALID);  // unreachable for a correct split
+  }
+  if (first_warp) emit_children(a, nd, table, a.leaf_of[cls], unit, fanout, lane);
+}
+
+// COUNT: work counting (the evaluations executed go to a.exec_count[1]);
+// without it the counter is compiled out.
+template <bool COUNT>
 __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint32_t gwarps, uint32_t cap) {
   extern __shared__ uint64_t staged[];
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
   __shared__ uint32_t fill[kWarps][16];
+  __shared__ unsigned long long wexec[kWarps];  // work counting: evaluations per warp, flushed at exit
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (COUNT && lane == 0) wexec[warp] = 0;
   const uint32_t gid = warp / gwarps, wig = warp % gwarps;
   const uint32_t tig = wig * 32 + lane, gthreads = gwarps * 32;
   const bool leader = wig == 0 && lane == 0;
@@ -279,52 +369,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
       // search: the parameters live only for this scope, so the registers
       // of the search loops are not shared with the partition step's state
       const Node nd = a.split_in[idx];
-      const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
-      const uint64_t* table = a.table[cls];
-      const uint64_t w1 = table[kTableWords * nd.m + 1];
+      const uint32_t depth = nd.depth & kDepthMask;
+      const uint64_t* table = a.table[nd.depth >> 8];
       SplitParams sp;
-      sp.m = nd.m;
-      sp.unit = static_cast<uint32_t>(w1);
-      sp.fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
-      sp.bits = 32 - __clz(nd.m);
-      sp.magic = static_cast<uint32_t>((0x100000000ull + sp.unit - 1) / sp.unit);
-      const uint32_t fields = sp.fanout - 1;
-      sp.target = 0;
-      for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
-      sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
-      // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
-      int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
-      if (sp.fanout == 4 && nd.m == 4 * sp.unit && nd.m < 256) {
-        mode = 6;
-        sp.cum_target = sp.unit | (sp.unit << 8) | (sp.unit << 16);
-      } else if (sp.fanout >= 5 && nd.m == sp.fanout * sp.unit && sp.unit >= 2 && nd.m < 65536) {
-        const uint32_t nb = nd.m < 256 && fields * 8 <= 32 ? 8 : 32 - __clz(sp.unit);
-        if (fields * nb <= 32) {
-          mode = 7;
-          sp.confirm = (1u << nb) <= nd.m;
-          sp.nbits = nb;
-          sp.nmask = fields * nb == 32 ? ~0u : (1u << (fields * nb)) - 1;
-          sp.ntarget = 0;
-          for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * nb);
-        }
-      }
-      if (mode == 1 && sp.fanout * sp.unit != nd.m) {
-        sp.nbits = 32 - __clz(sp.unit);
-        if (fields * sp.nbits <= 32) {
-          mode = 5;
-          sp.nmask = fields * sp.nbits == 32 ? ~0u : (1u << (fields * sp.nbits)) - 1;
-          sp.ntarget = 0;
-          for (uint32_t t = 0; t < fields; t++) sp.ntarget |= sp.unit << (t * sp.nbits);
-        }
-      }
-      if (nd.m < 65536 && sp.fanout >= 2 && sp.fanout <= kMaxThresholdFanout && fields * sp.bits <= 32) {
-        mode = 1 + static_cast<int>(sp.fanout);
-        // T_k = ceil(k * unit * 2^32 / m); field k - 1 must count k * unit keys
-        sp.thr1 = static_cast<uint32_t>(((uint64_t(sp.unit) << 32) + nd.m - 1) / nd.m);
-        sp.thr2 = static_cast<uint32_t>(((uint64_t(2 * sp.unit) << 32) + nd.m - 1) / nd.m);
-        sp.cum_target = sp.unit + (fields >= 2 ? (2 * sp.unit) << sp.bits : 0u);
-        sp.inc1 = 1u << sp.bits;
-      }
+      const int mode = split_setup(nd, table, sp);
       const uint64_t stall = stall_threshold(table, nd.m);
       const uint64_t limit = trial_limit(table, nd.m);
 
@@ -336,47 +384,221 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_level(SearchArgs a, uint3
       if (tig < 16) fill[gid][tig] = 0;
       group_sync(gid, gwarps);
 
+      unsigned long long* exec = COUNT ? &wexec[warp] : nullptr;
       if (in_smem)
-        split_search(mine, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+        split_search(mine, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error, exec);
       else
-        split_search(src, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error);
+        split_search(src, sp, mode, depth, wig, gwarps, lane, &best[gid], stall, limit, a.error, exec);
       group_sync(gid, gwarps);
     }
 
     const uint64_t seed = best[gid];
     if (!*reinterpret_cast<volatile int*>(a.error)) {
-      // the node again: partition its keys with the index found
       const Node nd = a.split_in[idx];
-      const uint32_t cls = nd.depth >> 8, depth = nd.depth & kDepthMask;
-      const uint64_t* table = a.table[cls];
-      const uint64_t w1 = table[kTableWords * nd.m + 1];
-      const uint32_t unit = static_cast<uint32_t>(w1), fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
-      const bool divide = nd.m >= 65536 || unit < 2;
-      const uint32_t magic = divide ? 0u : static_cast<uint32_t>((0x100000000ull + unit - 1) / unit);
-      const uint64_t* src = a.keys[depth & 1] + nd.start;
-      uint64_t* dst = a.keys[(depth + 1) & 1] + nd.start;
-      if (leader) {
-        a.seeds[nd.slot] = seed;
-        a.sizes[nd.slot] = nd.m;
-      }
-      // partition the keys into the children's ranges of the other array
-      const uint64_t kp = family_key(seed, depth);
-      const uint64_t* from = nd.m <= cap ? mine : src;
-      for (uint32_t j = tig; j < nd.m; j += gthreads) {
-        const uint64_t x = from[j];
-        const uint32_t v = phi_pre(x, kp, nd.m);
-        const uint32_t part = min(divide ? v / unit : __umulhi(v, magic), fanout - 1);
-        const uint32_t pos = atomicAdd(&fill[gid][part], 1u);
-        const uint32_t at = part * unit + pos;
-        if (at < nd.m)
-          dst[at] = x;
-        else
-          set_error(a.error, RECSPLIT_E_INVALID);  // unreachable for a correct split
-      }
-      if (wig == 0) emit_children(a, nd, table, a.leaf_of[cls], unit, fanout, lane);
+      partition_node(a, nd, seed, nd.m <= cap ? mine : nullptr, tig, gthreads, lane, wig == 0, fill[gid]);
     }
     group_sync(gid, gwarps);
   }
+  if (COUNT && lane == 0 && wexec[warp]) atomicAdd(a.exec_count + 1, wexec[warp]);
+}
+
+// ---------------------------------------------------------------- shared nodes
+// Levels whose nodes each need many trials (a node's expected work of
+// trials x keys is large, e.g. the 560 -> 5 x 112 and 112 -> 7 x 16 splits at
+// l = 16, b = 2000) end on a few long searches: trial counts are geometric,
+// so while the last nodes run, the CTAs that found the queue empty would sit
+// idle.  On these levels a CTA that finds the queue empty joins a node still
+// in progress instead.  Every participant's warps claim blocks of
+// kShareRounds * 32 consecutive indices from the node's block counter and
+// test them in order; a warp stops at its first success (atomicMin into the
+// node's best) or at a block that starts at or above the best.  Blocks are
+// claimed in increasing order, so every index below the final best was tested
+// and the result is the first successful index, whatever the participants.
+// The last participant to leave (refs drops to 0 and it closes the node)
+// partitions the keys and queues the children.
+constexpr uint32_t kShareRounds = 4;
+constexpr uint32_t kNodeOpen = 1, kNodeClosed = 2;
+constexpr uint32_t kMaxJoins = 4096;  // nodes one CTA may join in one launch
+
+// Returns the number of rounds of 32 indices the warp evaluated.
+template <int MODE>
+__device__ __forceinline__ uint32_t shared_search_warp(const uint64_t* __restrict__ keys, const SplitParams& sp,
+                                                       uint32_t depth, uint32_t lane, uint64_t* best,
+                                                       unsigned int* next, uint64_t stall, uint64_t limit,
+                                                       int* err) {
+  uint32_t blocks = 0, rounds = 0;
+  for (;;) {
+    uint32_t blk = 0;
+    if (lane == 0) blk = atomicAdd(next, 1u);
+    const uint64_t base0 = uint64_t(__shfl_sync(0xFFFFFFFFu, blk, 0)) * (kShareRounds * 32);
+    if (base0 >= volatile_load(best)) return rounds;
+    if ((++blocks & 63) == 0 && __shfl_sync(0xFFFFFFFFu, lane == 0 ? *reinterpret_cast<volatile int*>(err) : 0, 0))
+      return rounds;  // another search failed, or the host cancelled the build
+    // Blocks at or beyond the limit are not searched.  Participants claim
+    // ahead of the frontier, so a claim there does not mean the search
+    // failed: the node's closer reports the limit if no index below it
+    // succeeded (every block below it was then claimed and tested).
+    if (base0 >= limit) return rounds;
+    // the one warp whose block holds the stall point checks for keys that
+    // can never be separated (an O(m^2) scan, done once per node)
+    if (base0 <= stall && stall < base0 + kShareRounds * 32) {
+      if (has_duplicate(keys, sp.m, lane)) {
+        if (lane == 0) {
+          set_error(err, RECSPLIT_E_DUPLICATE);
+          atomicMin(reinterpret_cast<unsigned long long*>(best), 0ull);
+        }
+        return rounds;
+      }
+    }
+    for (uint32_t r = 0; r < kShareRounds; r++) {
+      const uint64_t base = base0 + r * 32;
+      if (r && base >= volatile_load(best)) return rounds;
+      const uint64_t kp = family_key(base + lane, depth);
+      bool ok = split_trial<MODE>(keys, sp, kp);
+      if ((MODE == 5 || (MODE == 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
+      const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+      rounds++;
+      if (hits) {
+        if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(best), base + __ffs(hits) - 1);
+        return rounds;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t shared_search(const uint64_t* __restrict__ keys, const SplitParams& sp, int mode,
+                                                  uint32_t depth, uint32_t lane, uint64_t* best, unsigned int* next,
+                                                  uint64_t stall, uint64_t limit, int* err) {
+  switch (mode) {
+    case 0: return shared_search_warp<0>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 1: return shared_search_warp<1>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 3: return shared_search_warp<3>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 4: return shared_search_warp<4>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 5: return shared_search_warp<5>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 6: return shared_search_warp<6>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 7: return shared_search_warp<7>(keys, sp, depth, lane, best, next, stall, limit, err);
+    default: return shared_search_warp<2>(keys, sp, depth, lane, best, next, stall, limit, err);
+  }
+}
+
+// One CTA per node at a time (all 8 warps); the node state arrays are sized
+// by the level's queue capacity, `flag` zeroed and `owned` (one entry per
+// CTA) set to ~0 before the launch.  A node takes at most cap[node] CTAs at
+// once: one per 2^12 expected trials, at most 16.
+template <bool COUNT>
+__global__ void __launch_bounds__(kThreads, 4) k_split_shared(SearchArgs a, SharedNodes st, uint32_t cap) {
+  extern __shared__ uint64_t mine[];
+  __shared__ uint32_t task, owner, closer, drained;
+  __shared__ uint32_t fill[16];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t total = *a.split_in_count;
+  volatile uint32_t* vflag = st.flag;
+  unsigned long long evals = 0;  // work counting: evaluations of this warp, flushed at exit
+  uint32_t joins = 0;            // nodes joined: bounded, so that the kernel ends whatever the timing
+  if (threadIdx.x == 0) drained = 0;
+  __syncthreads();
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      uint32_t idx = total, own = 0;
+      if (!*reinterpret_cast<volatile int*>(a.error) && !drained) {
+        const uint32_t i = atomicAdd(a.work_counter, 1u);
+        if (i < total) {
+          idx = i;
+          own = 1;
+          // participants worth having: about one CTA per 2^12 expected
+          // trials, at most 16 (a node of a few hundred trials gains nothing)
+          const Node nd = a.split_in[i];
+          const uint64_t et = a.table[nd.depth >> 8][kTableWords * nd.m + 2];
+          st.best[i] = ~0ull;
+          st.next[i] = 0;
+          st.refs[i] = 1;
+          st.cap[i] = static_cast<uint32_t>(min(uint64_t(16), max(uint64_t(1), et >> 12)));
+          __threadfence();
+          vflag[i] = kNodeOpen;
+          reinterpret_cast<volatile uint32_t*>(st.owned)[blockIdx.x] = i;
+        } else {
+          drained = 1;
+        }
+      }
+      task = idx;
+      owner = own;
+    }
+    __syncthreads();
+    if (task >= total && drained && warp == 0 && joins < kMaxJoins && !*reinterpret_cast<volatile int*>(a.error)) {
+      joins++;
+      // join the open node with the fewest participants, if any
+      for (int attempt = 0; attempt < 8; attempt++) {
+        uint32_t pick = total, fewest = ~0u;
+        for (uint32_t k0 = 0; k0 < gridDim.x; k0 += 32) {
+          const uint32_t k = k0 + lane;
+          const uint32_t j = k < gridDim.x ? reinterpret_cast<volatile uint32_t*>(st.owned)[k] : ~0u;
+          uint32_t r = ~0u;
+          if (j < total && vflag[j] == kNodeOpen) {
+            const uint32_t refs = reinterpret_cast<volatile uint32_t*>(st.refs)[j];
+            if (refs < reinterpret_cast<volatile uint32_t*>(st.cap)[j]) r = refs;
+          }
+          // smallest (refs, node) over the warp
+          unsigned long long key = (static_cast<unsigned long long>(r) << 32) | (j < total ? j : 0xFFFFFFFFu);
+          for (int o = 16; o; o >>= 1) key = min(key, __shfl_xor_sync(0xFFFFFFFFu, key, o));
+          if ((key >> 32) < fewest) {
+            fewest = static_cast<uint32_t>(key >> 32);
+            pick = static_cast<uint32_t>(key);
+          }
+        }
+        if (fewest == ~0u || pick >= total) break;
+        bool ok = false;
+        if (lane == 0) {
+          atomicAdd(&st.refs[pick], 1u);
+          __threadfence();
+          ok = vflag[pick] == kNodeOpen;
+          if (!ok) atomicSub(&st.refs[pick], 1u);  // closed meanwhile
+        }
+        if (__shfl_sync(0xFFFFFFFFu, ok, 0)) {
+          if (lane == 0) task = pick;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t idx = task;
+    if (idx >= total) break;
+    const Node nd = a.split_in[idx];
+    const uint32_t depth = nd.depth & kDepthMask;
+    const uint64_t* table = a.table[nd.depth >> 8];
+    const uint64_t* src = a.keys[depth & 1] + nd.start;
+    const bool in_smem = nd.m <= cap;
+    if (in_smem)
+      for (uint32_t j = threadIdx.x; j < nd.m; j += kThreads) mine[j] = src[j];
+    if (threadIdx.x < 16) fill[threadIdx.x] = 0;
+    __syncthreads();
+    {
+      SplitParams sp;
+      const int mode = split_setup(nd, table, sp);
+      const uint32_t rounds = shared_search(in_smem ? mine : src, sp, mode, depth, lane, &st.best[idx], &st.next[idx],
+                                            stall_threshold(table, nd.m), trial_limit(table, nd.m), a.error);
+      if (COUNT) evals += uint64_t(rounds) * 32 * nd.m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // leave; the last participant closes the node and partitions it
+      __threadfence();
+      const uint32_t left = atomicSub(&st.refs[idx], 1u);
+      closer = left == 1 && atomicCAS(&st.flag[idx], kNodeOpen, kNodeClosed) == kNodeOpen;
+      if (owner) reinterpret_cast<volatile uint32_t*>(st.owned)[blockIdx.x] = ~0u;
+    }
+    __syncthreads();
+    if (closer) {
+      const uint64_t seed = volatile_load(&st.best[idx]);
+      if (seed == ~0ull) {
+        if (threadIdx.x == 0) set_error(a.error, RECSPLIT_E_SEARCH_LIMIT);
+      } else if (!*reinterpret_cast<volatile int*>(a.error)) {
+        partition_node(a, nd, seed, in_smem ? mine : nullptr, threadIdx.x, kThreads, lane, warp == 0, fill);
+      }
+    }
+    __syncthreads();
+  }
+  if (COUNT && lane == 0 && evals) atomicAdd(a.exec_count + 1, evals);
 }
 
 // ---------------------------------------------------------------- leaves
@@ -394,54 +616,87 @@ __device__ __forceinline__ bool leaf_trial_full(const uint64_t (&x)[L], uint64_t
   return seen == (L == 32 ? ~0u : ((1u << L) - 1));
 }
 
+// The family key of index i at depth d, (i * 64 + d) * W, is i * 64W + d W:
+// a lane's keys for indices 32 apart differ by 32 * 64W, one 64-bit add.
+constexpr uint64_t kWeyl64 = kWeyl << 6;
+constexpr uint64_t kLaneStep = kWeyl64 * 32;
+
+__device__ __forceinline__ uint64_t index_key(uint64_t index, uint64_t dkey) { return index * kWeyl64 + dkey; }
+
 // Two-phase round of a warp over the indices base + j * 32 + lane, j < spl,
 // for a leaf of exactly L keys.  Phase 1 maps the first H keys: an index whose
 // first H values are not distinct cannot be a bijection.  The survivors are
 // compacted, in index order, into the warp's shared buffer with their
-// partial one-hot sums (H one bits); phase 2 finishes them on the last L - H
-// keys, 32 at a time.  The first survivor that completes 2^L - 1 is the smallest
-// bijective index of the round.  Returns it, or ~0 if the round has none.
-__host__ __device__ constexpr int leaf_first_half(int l) { return (l + 1) / 2; }
+// partial one-hot sums (H one bits) and their pre-shifted keys; phase 2
+// finishes them on the last L - H keys, 32 at a time.  The first survivor
+// that completes 2^L - 1 is the smallest bijective index of the round.
+// Returns it, or ~0 if the round has none.  With `exec` set, the
+// evaluations the round executed are added to it (work counting).
+//
+// H minimises the expected work per index, H + P_H (L - H) evaluations plus
+// the compaction and reload of a survivor (costed as 2.5 evaluations), with
+// P_H = L! / ((L - H)! L^H) the probability that the first H values are
+// distinct: 5 of 8 keys, 7 of 12, 8 of 16, 10 of 24.
+__host__ __device__ constexpr int leaf_first_part(int l) {
+  double p = 1.0, best = 1e30;
+  int arg = 1;
+  for (int h = 1; h < l; h++) {
+    const double cost = h + p * (l - h) + 2.5 * p;
+    if (cost < best) {
+      best = cost;
+      arg = h;
+    }
+    p = p * (l - h) / l;
+  }
+  return arg;
+}
 constexpr uint32_t kMaxSpl = 8;
 
 template <int L>
-__device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L], uint64_t base, uint32_t depth,
-                                                         uint32_t spl, uint32_t lane, uint2* surv) {
-  constexpr int H = leaf_first_half(L);
+__device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L], uint64_t base, uint64_t dkey,
+                                                         uint32_t spl, uint32_t lane, uint4* surv,
+                                                         unsigned long long* exec) {
+  constexpr int H = leaf_first_part(L);
   constexpr uint32_t full = L == 32 ? ~0u : ((1u << L) - 1);
+  const uint32_t below = (1u << lane) - 1;
   uint32_t nsurv = 0;
-  for (uint32_t j = 0; j < spl; j++) {
-    const uint32_t off = j * 32 + lane;
-    const uint64_t kp = family_key(base + off, depth);
+  uint64_t k = index_key(base + lane, dkey);
+  for (uint32_t j = 0; j < spl; j++, k += kLaneStep) {
+    const uint64_t kp = k ^ (k >> 30);
     uint32_t seen = 0;
 #pragma unroll
     for (int i = 0; i < H; i++) seen += 1u << phi_fixed<L>(x[i], kp);
     const bool ok = __popc(seen) == H;
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
-    if (ok) surv[nsurv + __popc(b & ((1u << lane) - 1))] = make_uint2(off, seen);
+    if (ok)
+      surv[nsurv + __popc(b & below)] =
+          make_uint4(j * 32 + lane, seen, static_cast<uint32_t>(kp), static_cast<uint32_t>(kp >> 32));
     nsurv += __popc(b);
   }
   __syncwarp();
+  uint64_t win = ~0ull;
+  uint32_t done = 0;
   for (uint32_t t0 = 0; t0 < nsurv; t0 += 32) {
     const uint32_t t = t0 + lane;
     bool ok = false;
     if (t < nsurv) {
-      const uint2 e = surv[t];
-      const uint64_t kp = family_key(base + e.x, depth);
+      const uint4 e = surv[t];
+      const uint64_t kp = (uint64_t(e.w) << 32) | e.z;
       uint32_t seen = e.y;
 #pragma unroll
       for (int i = H; i < L; i++) seen += 1u << phi_fixed<L>(x[i], kp);
       ok = seen == full;
     }
+    done = min(nsurv, t0 + 32);
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
     if (b) {
-      const uint64_t win = base + surv[t0 + __ffs(b) - 1].x;
-      __syncwarp();
-      return win;
+      win = base + surv[t0 + __ffs(b) - 1].x;
+      break;
     }
   }
+  if (exec && lane == 0) *exec += spl * 32 * H + done * (L - H);
   __syncwarp();
-  return ~0ull;
+  return win;
 }
 
 // Leaf of m < LMAX keys: slots j >= m contribute nothing.
@@ -478,9 +733,12 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
                                                                             uint32_t qfull) {
   __shared__ uint64_t best[kWarps];
   __shared__ uint32_t task[kWarps];
+  __shared__ unsigned long long wexec[kWarps];  // work counting: evaluations per warp, flushed at exit
   constexpr bool kTwoPhase = FULL && TWO && LMAX >= 4;
-  __shared__ uint2 surv[kTwoPhase ? kWarps : 1][kTwoPhase ? 32 * kMaxSpl : 1];
+  __shared__ uint4 surv[kTwoPhase ? kWarps : 1][kTwoPhase ? 32 * kMaxSpl : 1];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long* const exec = a.exec_count ? &wexec[warp] : nullptr;
+  if (lane == 0) wexec[warp] = 0;
   const uint32_t gid = warp / gwarps, wig = warp % gwarps;
   const bool leader = wig == 0 && lane == 0;
   const bool from_full = FULL || (RANGE && qfull);
@@ -511,6 +769,7 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
       group_sync(gid, gwarps);
       const uint64_t stall = stall_threshold(table, m);
       const uint64_t limit = trial_limit(table, m);
+      const uint64_t dkey = uint64_t(depth) * kWeyl;
       bool checked = false;
       uint32_t rounds = 0;
       // a round of a warp covers the spl * 32 indices from base; lane L tests
@@ -545,16 +804,19 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
         }
         uint64_t found = ~0ull;
         if (kTwoPhase) {
-          found = leaf_round_two_phase<LMAX>(x, base, depth, spl, lane, surv[warp]);
+          found = leaf_round_two_phase<LMAX>(x, base, dkey, spl, lane, surv[warp], exec);
         } else {
-          for (uint32_t j = 0; j < spl; j++) {
-            const uint64_t kp = family_key(base + j * 32 + lane, depth);
+          uint64_t k = index_key(base + lane, dkey);
+          for (uint32_t j = 0; j < spl; j++, k += kLaneStep) {
+            const uint64_t kp = k ^ (k >> 30);
             const bool ok = RANGE  ? leaf_trial_range<LMAX>(x, keep, m, m + extra, kp)
                             : FULL ? leaf_trial_full<LMAX>(x, kp)
                                    : leaf_trial_part<LMAX>(x, keep, m, kp);
             const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
             if (hits && found == ~0ull) found = base + j * 32 + __ffs(hits) - 1;
           }
+          // every slot of the kernel's LMAX is evaluated (masked beyond m)
+          if (exec && lane == 0) *exec += spl * 32 * LMAX;
         }
         if (found != ~0ull) {
           if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), found);
@@ -569,6 +831,7 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
       group_sync(gid, gwarps);
     }
   }
+  if (exec && lane == 0 && wexec[warp]) atomicAdd(a.exec_count, wexec[warp]);
 }
 
 template <typename K>
@@ -641,7 +904,25 @@ void set_tuning_for(uint32_t leaf, const recsplit_tuning_t& t) {
   g_tuned[leaf] = true;
 }
 
-int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s) {
+int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, int sm_count, cudaStream_t s,
+                       const SharedNodes* share) {
+  if (share) {
+    // one CTA per node at a time, nodes shared once the queue is empty
+    const size_t budget = 96 * 1024;
+    const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(max_m, budget / sizeof(uint64_t)));
+    const size_t smem = cap * sizeof(uint64_t);
+    auto kern = a.exec_count ? k_split_shared<true> : k_split_shared<false>;
+    RS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int blocks = 0;
+    int rc = persistent_grid(kern, smem, sm_count, &blocks);
+    if (rc) return rc;
+    blocks = std::min<int>(blocks, kSharedCtas);
+    RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
+    kern<<<blocks, kThreads, smem, s>>>(a, *share, static_cast<uint32_t>(cap));
+    count_launch();
+    RS_CUDA(cudaGetLastError());
+    return RECSPLIT_OK;
+  }
   // heavier nodes get more warps: fewer nodes per level and longer searches
   const recsplit_tuning_t t = tuning_for(max_leaf);
   const uint32_t gwarps = t.split_warps[max_m >= 256 ? 2 : (max_m >= 64 ? 1 : 0)];
@@ -650,12 +931,13 @@ int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, i
   uint64_t cap = std::min<uint64_t>(max_m, budget / (groups * sizeof(uint64_t)));
   if (cap < 1) cap = 1;
   const size_t smem = size_t(groups) * cap * sizeof(uint64_t);
-  RS_CUDA(cudaFuncSetAttribute(k_split_level, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  auto kern = a.exec_count ? k_split_level<true> : k_split_level<false>;
+  RS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int blocks = 0;
-  int rc = persistent_grid(k_split_level, smem, sm_count, &blocks);
+  int rc = persistent_grid(kern, smem, sm_count, &blocks);
   if (rc) return rc;
   RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
-  k_split_level<<<blocks, kThreads, smem, s>>>(a, gwarps, static_cast<uint32_t>(cap));
+  kern<<<blocks, kThreads, smem, s>>>(a, gwarps, static_cast<uint32_t>(cap));
   count_launch();
   RS_CUDA(cudaGetLastError());
   return RECSPLIT_OK;

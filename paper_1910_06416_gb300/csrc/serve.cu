@@ -2,18 +2,24 @@
 // of different sizes as they arrive and keeps the built structures resident
 // in device memory.
 //
-// Continuous batching: two worker threads own one stream each.
-//  - The build worker, whenever it is free, admits the waiting builds in
-//    arrival order for as long as their estimated device footprint fits the
-//    memory budget next to the resident structures and the builds in flight,
-//    and runs all admitted builds as one multi-set build (every set keeps its
-//    own parameters, and the result of each set is the same as its build
-//    alone).  Builds that arrive meanwhile wait for the next round.
+// Continuous batching:
+//  - Several build workers (recsplit_server_config_t::build_workers) each
+//    take, whenever they are free, the waiting builds in arrival order for as
+//    long as their estimated device footprint fits the memory budget next to
+//    the resident structures and every build in flight, and run them as one
+//    multi-set build (every set keeps its own parameters, and the result of
+//    each set is the same as its build alone).  A build that arrives while
+//    another round runs is taken by a free worker at once, and its kernels
+//    run beside that round's on the device.  Rounds of fewer than
+//    kSmallRound keys go on a stream of higher priority than larger ones, so
+//    when a long round's current kernel ends, the short round's kernels are
+//    scheduled first.
 //  - The lookup worker drains all waiting lookups into one batched lookup
-//    launch over the structures they name.  Lookups run on their own stream
-//    and overlap the builds on the device.
+//    launch over the structures they name, on the stream of the highest
+//    priority, overlapping the builds.
 // Each request records its queueing time and its latency (submission to
 // completion, host clock); completions are collected with poll.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -69,6 +75,9 @@ uint64_t build_footprint(uint64_t n, uint64_t total_bytes, uint32_t leaf, uint32
 
 }  // namespace
 
+// Rounds of fewer keys than this run on a build stream of higher priority.
+constexpr uint64_t kSmallRound = 1ull << 18;
+
 struct Server {
   // (recsplit_server_t)
   recsplit_server_config_t cfg;
@@ -81,8 +90,10 @@ struct Server {
   uint64_t in_flight = 0, resident_total = 0, next_id = 1;
   uint64_t served_keys = 0, served_queries = 0;
   bool stop = false;
-  std::thread tb, tl;
-  cudaStream_t sb = nullptr, sl = nullptr;
+  std::vector<std::thread> tb;
+  std::thread tl;
+  std::vector<cudaStream_t> sb_small, sb_large;  // per build worker
+  cudaStream_t sl = nullptr;
 
   void complete(const Req& r, int status, uint64_t items, uint32_t batch) {
     recsplit_completion_t c{};
@@ -98,14 +109,21 @@ struct Server {
   }
 
   // ------------------------------------------------------------ builds
-  void build_loop() {
+  void build_loop(uint32_t worker) {
     cudaSetDevice(device);
     for (;;) {
       std::vector<Req> batch;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_build.wait(lk, [&] { return stop || !builds.empty(); });
+        // wake for a build that fits next to the builds in flight (or that
+        // cannot fit even alone, to fail it); a round that ends or a release
+        // notifies
+        cv_build.wait(lk, [&] {
+          return stop || (!builds.empty() &&
+                          (in_flight == 0 || resident_total + in_flight + builds.front().footprint <= cfg.hbm_budget_bytes));
+        });
         if (stop && builds.empty()) return;
+        if (builds.empty()) continue;
         while (!builds.empty() && batch.size() < cfg.max_build_batch) {
           Req& r = builds.front();
           const bool fits = resident_total + in_flight + r.footprint <= cfg.hbm_budget_bytes;
@@ -125,10 +143,14 @@ struct Server {
       }
       if (batch.empty()) continue;
       const double t0 = now_ms();
-      for (Req& r : batch) r.t_start = t0;
+      uint64_t keys = 0;
+      for (Req& r : batch) {
+        r.t_start = t0;
+        keys += r.n;
+      }
       std::vector<int> status(batch.size(), RECSPLIT_OK);
       std::vector<Handle*> hs(batch.size(), nullptr);
-      run_builds(batch, 0, batch.size(), status, hs);
+      run_builds(batch, 0, batch.size(), status, hs, keys < kSmallRound ? sb_small[worker] : sb_large[worker]);
       std::lock_guard<std::mutex> lk(mu);
       for (size_t i = 0; i < batch.size(); i++) {
         in_flight -= batch[i].footprint;
@@ -147,7 +169,8 @@ struct Server {
 
   // Builds batch[a, b) together; if that fails, each set alone, so that one
   // bad request (e.g. repeated keys) fails only itself.
-  void run_builds(std::vector<Req>& batch, size_t a, size_t b, std::vector<int>& status, std::vector<Handle*>& hs) {
+  void run_builds(std::vector<Req>& batch, size_t a, size_t b, std::vector<int>& status, std::vector<Handle*>& hs,
+                  cudaStream_t sb) {
     std::vector<void*> staged;
     std::vector<SetInput> sets(b - a);
     int rc = RECSPLIT_OK;
@@ -188,7 +211,7 @@ struct Server {
     for (void* p : staged) cudaFreeAsync(p, sb);
     cudaStreamSynchronize(sb);
     if (rc && b - a > 1) {
-      for (size_t i = a; i < b; i++) run_builds(batch, i, i + 1, status, hs);
+      for (size_t i = a; i < b; i++) run_builds(batch, i, i + 1, status, hs, sb);
       return;
     }
     for (size_t i = a; i < b; i++) status[i] = rc;
@@ -330,20 +353,33 @@ int recsplit_server_create(const recsplit_server_config_t* cfg, recsplit_server_
   s->cfg.hbm_budget_bytes = cfg && cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (64ull << 30);
   s->cfg.max_build_batch = cfg && cfg->max_build_batch ? cfg->max_build_batch : 64;
   s->cfg.max_lookup_batch = cfg && cfg->max_lookup_batch ? cfg->max_lookup_batch : (64ull << 20);
-  // Lookups run on a stream of the highest priority and builds on one of the
-  // lowest: the searches are persistent kernels that hold every SM for one
-  // tree level, so a lookup arriving during a build waits at most for the
-  // level in progress instead of for the rest of the build.
+  s->cfg.build_workers = cfg && cfg->build_workers ? std::min<uint32_t>(cfg->build_workers, 16) : 3;
+  // Lookups run on a stream of the highest priority, short build rounds on
+  // one of a middle priority and long ones on one of the lowest: the searches
+  // are persistent kernels that hold every SM for one tree level, so a lookup
+  // or a short build arriving during a long build waits for the kernel in
+  // progress, not for the rest of the build.
   int least = 0, greatest = 0;
-  if (cudaGetDevice(&s->device) != cudaSuccess ||
-      cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&s->sb, cudaStreamNonBlocking, least) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&s->sl, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+  bool ok = cudaGetDevice(&s->device) == cudaSuccess &&
+            cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&s->sl, cudaStreamNonBlocking, greatest) == cudaSuccess;
+  const int middle = greatest < least ? greatest + 1 : greatest;
+  for (uint32_t w = 0; ok && w < s->cfg.build_workers; w++) {
+    cudaStream_t a = nullptr, b = nullptr;
+    ok = cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, middle) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, least) == cudaSuccess;
+    if (a) s->sb_small.push_back(a);
+    if (b) s->sb_large.push_back(b);
+  }
+  if (!ok) {
     int rc = rs::cuda_fail(cudaGetLastError(), "server streams");
+    for (cudaStream_t x : s->sb_small) cudaStreamDestroy(x);
+    for (cudaStream_t x : s->sb_large) cudaStreamDestroy(x);
+    if (s->sl) cudaStreamDestroy(s->sl);
     delete s;
     return rc;
   }
-  s->tb = std::thread([s] { s->build_loop(); });
+  for (uint32_t w = 0; w < s->cfg.build_workers; w++) s->tb.emplace_back([s, w] { s->build_loop(w); });
   s->tl = std::thread([s] { s->lookup_loop(); });
   *out = reinterpret_cast<recsplit_server_t*>(s);
   return RECSPLIT_OK;
@@ -358,10 +394,11 @@ void recsplit_server_destroy(recsplit_server_t* sp) {
   }
   s->cv_build.notify_all();
   s->cv_lookup.notify_all();
-  s->tb.join();
+  for (std::thread& t : s->tb) t.join();
   s->tl.join();
   for (auto& kv : s->resident) delete kv.second.h;
-  cudaStreamDestroy(s->sb);
+  for (cudaStream_t x : s->sb_small) cudaStreamDestroy(x);
+  for (cudaStream_t x : s->sb_large) cudaStreamDestroy(x);
   cudaStreamDestroy(s->sl);
   delete s;
 }

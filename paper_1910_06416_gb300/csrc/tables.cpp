@@ -98,7 +98,9 @@ int build_tables(uint32_t leaf, uint32_t extra, uint64_t mmax, Tables* T, std::s
   T->codes.assign(mmax + 1, 0);
   T->expected_trials.assign(mmax + 1, 0);
   T->range.assign(mmax + 1, 0);
-  T->device_words.assign(kTableWords * (mmax + 1), 0);
+  // the search tables, then the lookup records (two words per size)
+  T->device_words.assign((kTableWords + 2) * (mmax + 1), 0);
+  LookupRecord* rec = reinterpret_cast<LookupRecord*>(T->device_words.data() + kTableWords * (mmax + 1));
   // sizes 0 and 1: no code, output range m
   T->range[1] = 1;
   T->device_words[kTableWords * 1 + 3] = uint64_t(1) << 32;
@@ -139,6 +141,16 @@ int build_tables(uint32_t leaf, uint32_t extra, uint64_t mmax, Tables* T, std::s
       if ((m - 1) * (M * sh.unit - (1ull << 32)) < (1ull << 32)) magic = M;
     }
     T->device_words[kTableWords * m + 3] = magic | (T->range[m] << 32);
+    const uint64_t unit_codes = sh.fanout ? T->codes[sh.unit] : 0;
+    if (unit_codes >= (1ull << kLookupCodeBits) || sh.fanout >= 16) {
+      if (err) *err = "node size too large for the lookup records";
+      return RECSPLIT_E_INVALID;
+    }
+    rec[m].unit = static_cast<uint32_t>(sh.unit);
+    rec[m].magic = static_cast<uint32_t>(magic);
+    rec[m].fixed = static_cast<uint32_t>(sh.fanout ? T->fixed_bits[sh.unit] : 0);
+    rec[m].info = static_cast<uint32_t>(unit_codes) | (static_cast<uint32_t>(r) << kLookupCodeBits) |
+                  (sh.fanout << 28);
   }
   return RECSPLIT_OK;
 }

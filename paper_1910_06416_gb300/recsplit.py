@@ -39,7 +39,8 @@ class Profile(C.Structure):
                 ("ms_leaf", C.c_double), ("ms_encode", C.c_double), ("ms_total", C.c_double),
                 ("split_nodes", C.c_uint64), ("split_trials", C.c_uint64), ("split_evals", C.c_uint64),
                 ("leaf_nodes", C.c_uint64), ("leaf_trials", C.c_uint64), ("leaf_evals", C.c_uint64),
-                ("launches", C.c_uint32), ("split_levels", C.c_uint32)]
+                ("launches", C.c_uint32), ("split_levels", C.c_uint32),
+                ("leaf_evals_executed", C.c_uint64), ("split_evals_executed", C.c_uint64)]
 
 
 class KeySet(C.Structure):
@@ -49,7 +50,8 @@ class KeySet(C.Structure):
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_build_batch", C.c_uint32), ("max_lookup_batch", C.c_uint64)]
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_build_batch", C.c_uint32), ("max_lookup_batch", C.c_uint64),
+                ("build_workers", C.c_uint32)]
 
 
 class Completion(C.Structure):
@@ -337,8 +339,8 @@ def recsplit_autotune(leaf_size: int, bucket_size: int, sample_keys: int = 1 << 
 
 
 # ---------------------------------------------------------------- serving
-def recsplit_server_create(hbm_budget_bytes=0, max_build_batch=0, max_lookup_batch=0) -> int:
-    cfg = ServerConfig(hbm_budget_bytes, max_build_batch, max_lookup_batch)
+def recsplit_server_create(hbm_budget_bytes=0, max_build_batch=0, max_lookup_batch=0, build_workers=0) -> int:
+    cfg = ServerConfig(hbm_budget_bytes, max_build_batch, max_lookup_batch, build_workers)
     h = C.c_void_p()
     _check(lib().recsplit_server_create(C.byref(cfg), C.byref(h)), "recsplit_server_create")
     return h.value

@@ -103,3 +103,37 @@ def test_memory_budget_admission(rs):
         assert all(np.array_equal(b, blobs[0]) for b in blobs)
     finally:
         rs.recsplit_server_destroy(srv)
+
+
+def test_short_build_overtakes_a_long_one(rs):
+    """A 10^4-key build submitted while a long build runs (10^6 keys, l = 16,
+    b = 2000, about a second) is taken by a free build worker at once and
+    completes first; both structures equal the same builds served alone."""
+    big = inputs.u64_keys(1_000_000, 2)
+    small = inputs.byte_keys(10_000, 41)
+    srv = rs.recsplit_server_create(hbm_budget_bytes=8 << 30)
+    try:
+        big_id = rs.recsplit_server_submit_build_u64(srv, big, 16, 2000)
+        t0 = time.time()
+        while rs.recsplit_server_stats(srv)["in_flight_bytes"] == 0 and time.time() - t0 < 10:
+            time.sleep(0.001)
+        time.sleep(0.05)  # the long build is on the device
+        small_id = rs.recsplit_server_submit_build_bytes(srv, small.data, small.offsets, 8, 100)
+        order = []
+        got = {}
+        while len(got) < 2 and time.time() - t0 < 120:
+            for c in rs.recsplit_server_poll(srv, 16, wait_ms=20):
+                got[c["request_id"]] = c
+                order.append(c["request_id"])
+        assert order == [small_id, big_id], order
+        assert got[small_id]["status"] == 0 and got[big_id]["status"] == 0
+        assert got[small_id]["batch_size"] == 1
+        assert got[small_id]["queue_ms"] < 100
+        alone_small = rs.Structure.build_bytes(small.data, small.offsets, 8, 100)
+        assert np.array_equal(rs.recsplit_serialize(rs.recsplit_server_structure(srv, small_id)),
+                              alone_small.serialize())
+        alone_big = rs.Structure.build_u64(big, 16, 2000)
+        assert np.array_equal(rs.recsplit_serialize(rs.recsplit_server_structure(srv, big_id)),
+                              alone_big.serialize())
+    finally:
+        rs.recsplit_server_destroy(srv)

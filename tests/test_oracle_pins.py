@@ -470,6 +470,23 @@ def test_bits_per_key_match_paper(orc, row):
     assert abs(orc.bits_per_key(blob) - want) < 0.05, (orc.bits_per_key(blob), want)
 
 
+def test_space_optimal_row_matches_paper(orc):
+    """Table 1's space-optimal row, l = 16, b = 2000: 1.56 bits/key.  The
+    oracle needs about half an hour of host time for 10^6 keys at this leaf
+    size, so its structure of the 10^6 keys (seed 2) is summarised in a file
+    written by tests/golden/make_oracle_digests.py, which calls the oracle
+    alone; here its bits/key must print as the paper's two decimals, and its
+    tree bits/key must follow the Sec. 5.4 expected-length model."""
+    import json
+    with open(os.path.join(GOLDEN, "oracle_digests_c3.json")) as f:
+        c3 = json.load(f)
+    assert (c3["config"]["leaf"], c3["config"]["bucket"], c3["config"]["n"]) == (16, 2000, 1000000)
+    row = [r for r in _golden_rows("paper_bits_per_key.txt") if (int(r[0]), int(r[1])) == (16, 2000)][0]
+    assert round(c3["bits_per_key"], 2) == float(row[3]), (c3["bits_per_key"], row)
+    want = _expected_tree_bits_per_key(orc, 16, 2000)
+    assert abs(c3["tree_bits"] / c3["config"]["n"] - want) < 0.02, (c3["tree_bits"] / c3["config"]["n"], want)
+
+
 def test_decoded_seeds_equal_per_bucket_search(orc):
     n, leaf, b = 20000, 8, 100
     keys = inputs.u64_keys(n, 21)
