@@ -296,13 +296,22 @@ def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5):
     rs.recsplit_server_destroy(srv)
     res = {"seconds": wall, "rate_hz": rate, "requests": len(done)}
     for kind, name in ((0, "build"), (1, "lookup")):
-        lat = np.array([c["latency_ms"] for c in done if c["kind"] == kind and c["status"] == 0])
-        items = sum(c["items"] for c in done if c["kind"] == kind and c["status"] == 0)
+        ok = [c for c in done if c["kind"] == kind and c["status"] == 0]
+        lat = np.array([c["latency_ms"] for c in ok])
+        qms = np.array([c["queue_ms"] for c in ok])
+        items = sum(c["items"] for c in ok)
         res[name] = {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
                      "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                     "queue_p50_ms": float(np.percentile(qms, 50)) if qms.size else None,
+                     "queue_p99_ms": float(np.percentile(qms, 99)) if qms.size else None,
                      "items_per_s": items / wall,
                      "mean_batch": float(np.mean([c["batch_size"] for c in done if c["kind"] == kind] or [0]))}
-    res["failed"] = sum(1 for c in done if c["status"] != 0)
+    failed = [c for c in done if c["status"] != 0]
+    res["failed"] = len(failed)
+    res["failed_by"] = {}
+    for c in failed:
+        key = f'{"build" if c["kind"] == 0 else "lookup"} {rs.recsplit_strerror(c["status"])}'
+        res["failed_by"][key] = res["failed_by"].get(key, 0) + 1
     return res
 
 

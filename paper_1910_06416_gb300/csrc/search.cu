@@ -834,6 +834,31 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
   if (exec && lane == 0 && wexec[warp]) atomicAdd(a.exec_count, wexec[warp]);
 }
 
+// Dynamic shared memory the split kernels may use: nodes of up to this many
+// bytes of keys are staged, larger ones read from global memory.
+constexpr size_t kSplitSmemBudget = 96 * 1024;
+
+// Raises the kernel's dynamic shared memory limit to the budget, once per
+// kernel and process.  Setting it per launch to the launch's own size would
+// race between builds on several host threads (the serving engine's
+// workers): one thread could lower the limit between another's setting and
+// its launch, which would then fail.
+// (Once per kernel and device: KERNEL is the kernel itself, so every
+// instantiation keeps flags of its own.)
+template <auto KERNEL>
+int allow_split_smem() {
+  static std::once_flag once[64];
+  static cudaError_t status[64] = {};
+  int dev = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(RECSPLIT_E_INVALID, "device ordinal above 63");
+  std::call_once(once[dev], [&] {
+    status[dev] = cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSplitSmemBudget));
+  });
+  if (status[dev] != cudaSuccess) return cuda_fail(status[dev], "cudaFuncSetAttribute");
+  return RECSPLIT_OK;
+}
+
 template <typename K>
 int persistent_grid(K kernel, size_t smem, int sm_count, int* blocks) {
   int per_sm = 0;
@@ -908,13 +933,13 @@ int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, i
                        const SharedNodes* share) {
   if (share) {
     // one CTA per node at a time, nodes shared once the queue is empty
-    const size_t budget = 96 * 1024;
-    const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(max_m, budget / sizeof(uint64_t)));
+    const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(max_m, kSplitSmemBudget / sizeof(uint64_t)));
     const size_t smem = cap * sizeof(uint64_t);
     auto kern = a.exec_count ? k_split_shared<true> : k_split_shared<false>;
-    RS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int rc = a.exec_count ? allow_split_smem<k_split_shared<true>>() : allow_split_smem<k_split_shared<false>>();
+    if (rc) return rc;
     int blocks = 0;
-    int rc = persistent_grid(kern, smem, sm_count, &blocks);
+    rc = persistent_grid(kern, smem, sm_count, &blocks);
     if (rc) return rc;
     blocks = std::min<int>(blocks, kSharedCtas);
     RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
@@ -927,14 +952,14 @@ int launch_split_level(const SearchArgs& a, uint64_t max_m, uint32_t max_leaf, i
   const recsplit_tuning_t t = tuning_for(max_leaf);
   const uint32_t gwarps = t.split_warps[max_m >= 256 ? 2 : (max_m >= 64 ? 1 : 0)];
   const uint32_t groups = kWarps / gwarps;
-  const size_t budget = 96 * 1024;
-  uint64_t cap = std::min<uint64_t>(max_m, budget / (groups * sizeof(uint64_t)));
+  uint64_t cap = std::min<uint64_t>(max_m, kSplitSmemBudget / (groups * sizeof(uint64_t)));
   if (cap < 1) cap = 1;
   const size_t smem = size_t(groups) * cap * sizeof(uint64_t);
   auto kern = a.exec_count ? k_split_level<true> : k_split_level<false>;
-  RS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int rc = a.exec_count ? allow_split_smem<k_split_level<true>>() : allow_split_smem<k_split_level<false>>();
+  if (rc) return rc;
   int blocks = 0;
-  int rc = persistent_grid(kern, smem, sm_count, &blocks);
+  rc = persistent_grid(kern, smem, sm_count, &blocks);
   if (rc) return rc;
   RS_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(uint32_t), s));
   kern<<<blocks, kThreads, smem, s>>>(a, gwarps, static_cast<uint32_t>(cap));
