@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the space-optimal (l=16, b=2000) and batched (4096 sets) entries of the default run")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-workers", type=int, default=0, help="build workers of the serving engine (0: its default)")
     return ap.parse_args()
 
 
@@ -242,13 +243,13 @@ def cpu_baseline(a, keys_np):
                             "sample": f"{reps1} builds of the first {n1} keys on one thread in {dt1:.1f} s"}}
 
 
-def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5):
+def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5, workers=0):
     """Continuous-batching server under Poisson arrivals (mean `rate`/s):
     half builds of log-uniform 10^4..10^7 byte-string keys (slices of the
     key pool), half lookups of log-uniform 10^3..10^6 member queries against
     a resident structure.  Latency is submission to completion."""
     rng = np.random.default_rng(seed)
-    srv = rs.recsplit_server_create(hbm_budget_bytes=64 << 30)
+    srv = rs.recsplit_server_create(hbm_budget_bytes=64 << 30, build_workers=workers)
     npool = keys.n
     times, t = [], 0.0
     while True:
@@ -520,7 +521,8 @@ def run_ours(a):
                 "bits_per_key": stats["bits_per_key"], "roofline": roofline, "rooflines": rooflines, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks}
         if a.serve_seconds > 0:
-            line["serve"] = serve_run(rs, keys, a.serve_seconds, a.serve_rate, a.leaf, a.bucket)
+            line["serve"] = serve_run(rs, keys, a.serve_seconds, a.serve_rate, a.leaf, a.bucket,
+                                      workers=a.serve_workers)
         if not a.no_extras:
             del qdata, qoffs, qout
             torch.cuda.empty_cache()
@@ -696,17 +698,21 @@ def run_u64(a):
     del qidx
     out = torch.empty(a.queries, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    tuning = rs.recsplit_autotune(a.leaf, a.bucket, a.n, stream.cuda_stream)
+    tuning = tuned_shapes(rs, a.leaf, a.bucket, a.n, stream.cuda_stream)
     rs.recsplit_set_profiling(True)
     bt, lt, profs = [], [], []
     for step in range(a.warmup + a.steps):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        if step == a.warmup:
+            nvtx_push("timed")  # profilers can restrict a capture to the timed steps
         e0.record(stream)
         h = rs.recsplit_build_u64(keys, a.leaf, a.bucket, stream.cuda_stream)
         e1.record(stream)
         rs.recsplit_lookup_u64(h, queries, out, stream.cuda_stream)
         e2.record(stream)
         torch.cuda.synchronize()
+        if step == a.warmup + a.steps - 1:
+            nvtx_pop()
         if step >= a.warmup:
             bt.append(e0.elapsed_time(e1))
             lt.append(e1.elapsed_time(e2))

@@ -156,6 +156,15 @@ __device__ __forceinline__ uint32_t select_in_word64(uint64_t x, uint32_t k) {
   return (up ? 32u : 0u) + select_in_word32(up ? static_cast<uint32_t>(x >> 32) : lo, up ? k - c : k);
 }
 
+// The 64 bits of the code from bit pos (relative to t), zero past `end`.
+__device__ __forceinline__ uint64_t window64(const uint32_t* __restrict__ t, uint32_t pos, uint32_t end) {
+  const uint32_t w = pos >> 5, sh = pos & 31;
+  const uint32_t a0 = w < end ? __ldg(t + w) : 0u;
+  const uint32_t a1 = w + 1 < end ? __ldg(t + w + 1) : 0u;
+  const uint32_t a2 = w + 2 < end ? __ldg(t + w + 2) : 0u;
+  return (uint64_t(__funnelshift_r(a1, a2, sh)) << 32) | __funnelshift_r(a0, a1, sh);
+}
+
 // (i * 64 + d) * W = i * (64 W) + d * W: the family key of index i at depth d
 // as one multiply-add, the depth term advancing by W per level.
 constexpr uint64_t kWeyl64 = kWeyl << 6;
@@ -167,8 +176,10 @@ constexpr uint64_t kWeyl64 = kWeyl << 6;
 // subtree (to skip the earlier siblings).  The unary part of the bucket's
 // code (one code per node, about 1.5 bits each) is held in a 64-bit register
 // window from its first bit, so reading a unary code is a find-first-set and
-// skipping j * codes(unit) codes a select inside the window; a unary part that
-// runs past the window continues with scans of the code words.  Fixed parts
+// skipping j * codes(unit) codes a select inside the window.  Where the
+// window runs out (buckets of thousands of keys), a scan of the code words
+// finds the position and the window is reloaded there: the chosen subtree's
+// codes follow it, so the rest of the descent reads the new window.  Fixed parts
 // are read with two loads and a funnel shift, without a branch.
 __device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
   const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
@@ -177,14 +188,8 @@ __device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint
   uint32_t fixed = static_cast<uint32_t>(o & 31);
   // the unary part starts after the fixed parts of all the bucket's codes
   const uint32_t u0 = fixed + static_cast<uint32_t>(__ldg(v.table + kTableWords * m));
-  uint64_t win;
-  {
-    const uint32_t uw = u0 >> 5, us = u0 & 31;
-    const uint32_t a0 = __ldg(t + uw);
-    const uint32_t a1 = uw + 1 < end ? __ldg(t + uw + 1) : 0u;
-    const uint32_t a2 = uw + 2 < end ? __ldg(t + uw + 2) : 0u;
-    win = (uint64_t(__funnelshift_r(a1, a2, us)) << 32) | __funnelshift_r(a0, a1, us);
-  }
+  uint32_t wb = 0;  // first bit of the window, relative to u0
+  uint64_t win = window64(t, u0, end);
   uint32_t up = 0;  // bit of the next unary code, relative to u0
   const uint64_t xpre = pre_key(lo);
   uint64_t dkey = 0;  // depth * W
@@ -198,7 +203,8 @@ __device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint
     const uint32_t f1 = fw + 1 < end ? __ldg(t + fw + 1) : 0u;
     const uint32_t low = __funnelshift_r(f0, f1, fixed & 31) & ((1u << r) - 1u);
     fixed += r;
-    const uint64_t rest = up < 64 ? win >> up : 0ull;
+    const uint32_t rel = up - wb;
+    const uint64_t rest = rel < 64 ? win >> rel : 0ull;
     uint32_t one;  // the unary code's one bit, relative to u0
     if (rest) {
       one = up + static_cast<uint32_t>(__ffsll(static_cast<long long>(rest)) - 1);
@@ -206,6 +212,8 @@ __device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint
       const uint32_t a = code_next_one(t, u0 + up, end);
       if (a == ~0u) return ~0ull;
       one = a - u0;
+      wb = one;  // the rest of the descent reads from here on
+      win = window64(t, u0 + wb, end);
     }
     const uint64_t seed = (uint64_t(one - up) << r) | low;
     up = one + 1;
@@ -220,13 +228,16 @@ __device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint
       // one of rank part * codes(unit) - 1
       const uint32_t skip = part * (nd.w & ((1u << kLookupCodeBits) - 1));
       if (skip) {
-        const uint64_t x = up < 64 ? win & (~0ull << up) : 0ull;
+        const uint32_t rel = up - wb;
+        const uint64_t x = rel < 64 ? win & (~0ull << rel) : 0ull;
         if (static_cast<uint32_t>(__popcll(x)) >= skip) {
-          up = select_in_word64(x, skip - 1) + 1;
+          up = wb + select_in_word64(x, skip - 1) + 1;
         } else {
           const uint32_t a = code_select(t, u0 + up, skip - 1, end);
           if (a == ~0u) return ~0ull;
           up = a - u0 + 1;
+          wb = up;  // the chosen subtree's codes start here
+          win = window64(t, u0 + wb, end);
         }
       }
       c += part * nd.x;

@@ -487,6 +487,21 @@ def test_space_optimal_row_matches_paper(orc):
     assert abs(c3["tree_bits"] / c3["config"]["n"] - want) < 0.02, (c3["tree_bits"] / c3["config"]["n"], want)
 
 
+def test_table2_row_matches_paper():
+    """Table 2's l = 8, b = 100 row at 10^9 keys: 1.80 bits/key.  The
+    oracle's structure of 10^9 keys (seed 4) takes about 20 minutes and
+    45 GB of host memory, so its size is read from the summary written by
+    tests/golden/make_oracle_digests.py (oracle only) and must print as the
+    paper's two decimals."""
+    import json
+    with open(os.path.join(GOLDEN, "oracle_digests_big.json")) as f:
+        big = json.load(f)
+    assert (big["config"]["leaf"], big["config"]["bucket"], big["config"]["n"]) == (8, 100, 10 ** 9)
+    row = [r for r in _golden_rows("paper_bits_per_key.txt") if int(r[2]) == 10 ** 9][0]
+    assert (int(row[0]), int(row[1])) == (8, 100)
+    assert round(big["bits_per_key"], 2) == float(row[3]), (big["bits_per_key"], row)
+
+
 def test_decoded_seeds_equal_per_bucket_search(orc):
     n, leaf, b = 20000, 8, 100
     keys = inputs.u64_keys(n, 21)
