@@ -699,7 +699,7 @@ def run_u64(a):
     out = torch.empty(a.queries, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
     tuning = tuned_shapes(rs, a.leaf, a.bucket, a.n, stream.cuda_stream)
-    rs.recsplit_set_profiling(True)
+    rs.recsplit_set_profiling(2)  # phase events only in the timed builds
     bt, lt, profs = [], [], []
     for step in range(a.warmup + a.steps):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -719,20 +719,22 @@ def run_u64(a):
             profs.append(rs.recsplit_last_profile())
         stats = rs.recsplit_stats(h)
         rs.recsplit_free(h)
+    # the work counts (algorithmic and executed) from one more, untimed build
+    rs.recsplit_set_profiling(1)
+    rs.recsplit_free(rs.recsplit_build_u64(keys, a.leaf, a.bucket, stream.cuda_stream))
+    work = rs.recsplit_last_profile()
+    rs.recsplit_set_profiling(0)
+    prof = {k: statistics.median(p[k] for p in profs)
+            for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")}
     line = {"metric": "build keys/s (64-bit keys)", "value": a.n / (statistics.median(bt) / 1e3), "unit": "keys/s",
             "workload": "u64", "n": a.n, "leaf_size": a.leaf, "bucket_size": a.bucket, "seed": seed,
             "build_ms": statistics.median(bt), "lookup": {"value": a.queries / (statistics.median(lt) / 1e3),
                                                           "unit": "queries/s", "queries": a.queries},
-            "phases_ms": {k: statistics.median(p[k] for p in profs)
-                          for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")},
-            "work": {k: profs[-1][k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes",
-                                               "leaf_trials", "leaf_evals")},
-            "bits_per_key": stats["bits_per_key"], "tuning": tuning}
-    peak_ops = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
-    for kind, ops in (("leaf", OPS_PER_LEAF_EVAL), ("split", OPS_PER_SPLIT_EVAL)):
-        ms = line["phases_ms"][f"ms_{kind}"]
-        if ms > 0:
-            line[f"{kind}_search_frac_of_issue_peak"] = line["work"][f"{kind}_evals"] * ops / (ms / 1e3) / peak_ops
+            "phases_ms": prof,
+            "work": {k: work[k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes", "leaf_trials",
+                                          "leaf_evals", "split_evals_executed", "leaf_evals_executed")},
+            "bits_per_key": stats["bits_per_key"], "tuning": tuning,
+            "rooflines": search_rooflines(prof, work, SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
     if not a.no_cpu_baseline:
         from oracle import oracle
         threads = os.cpu_count() or 1

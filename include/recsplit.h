@@ -247,7 +247,7 @@ typedef struct recsplit_server_config {
   uint64_t hbm_budget_bytes;  /* device bytes for resident structures + builds in flight (0: 64 GiB) */
   uint32_t max_build_batch;   /* builds per device round (0: 64)                               */
   uint64_t max_lookup_batch;  /* queries per lookup launch (0: 2^26)                            */
-  uint32_t build_workers;     /* build rounds that may run at once (0: 3; at most 16)          */
+  uint32_t build_workers;     /* build rounds that may run at once (0: 6; at most 16)          */
 } recsplit_server_config_t;
 
 typedef struct recsplit_completion {

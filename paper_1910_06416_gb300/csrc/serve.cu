@@ -353,7 +353,7 @@ int recsplit_server_create(const recsplit_server_config_t* cfg, recsplit_server_
   s->cfg.hbm_budget_bytes = cfg && cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (64ull << 30);
   s->cfg.max_build_batch = cfg && cfg->max_build_batch ? cfg->max_build_batch : 64;
   s->cfg.max_lookup_batch = cfg && cfg->max_lookup_batch ? cfg->max_lookup_batch : (64ull << 20);
-  s->cfg.build_workers = cfg && cfg->build_workers ? std::min<uint32_t>(cfg->build_workers, 16) : 3;
+  s->cfg.build_workers = cfg && cfg->build_workers ? std::min<uint32_t>(cfg->build_workers, 16) : 6;
   // Lookups run on a stream of the highest priority, short build rounds on
   // one of a middle priority and long ones on one of the lowest: the searches
   // are persistent kernels that hold every SM for one tree level, so a lookup

@@ -66,11 +66,15 @@ def test_profiling_events_only_and_deterministic_work(rs):
 
 def test_executed_evaluation_counts(rs):
     """The work-counting build also counts the evaluations the searches
-    execute.  With one warp per node the count is deterministic, and it is
-    bounded by what the searches must do: every split trial evaluates all m
-    keys, rounded up to rounds of 32 indices; every leaf index tested
+    execute, bounded by what the searches must do: every split trial
+    evaluates all m keys, rounded up to rounds of 32 indices (with one warp
+    per node this count is the same in every build); every leaf index tested
     evaluates at least the first-phase keys (5 of 8) and at most all 8, and a
-    leaf tests at most one round (4 x 32 indices) past its first success."""
+    leaf tests at most one round (4 x 32 indices) past its first success.
+    The leaf count varies a little between builds: which keys of a leaf are
+    its first five depends on the order the partition's atomics wrote them
+    in, and with it how many indices survive the first phase (the index
+    found does not change)."""
     keys = torch.from_numpy(inputs.u64_keys(200_000, 6).view(np.int64)).cuda()
     saved = rs.recsplit_get_tuning(8)
     rs.recsplit_set_tuning(8, {"leaf_warps": 1, "leaf_chunk": 4, "leaf_seeds_per_lane": 4,
@@ -85,8 +89,8 @@ def test_executed_evaluation_counts(rs):
         rs.recsplit_set_profiling(0)
         rs.recsplit_set_tuning(8, saved)
     p = profs[0]
-    assert (p["leaf_evals_executed"], p["split_evals_executed"]) == \
-        (profs[1]["leaf_evals_executed"], profs[1]["split_evals_executed"])
+    assert p["split_evals_executed"] == profs[1]["split_evals_executed"]
+    assert abs(p["leaf_evals_executed"] - profs[1]["leaf_evals_executed"]) < 0.01 * p["leaf_evals_executed"]
     max_m = 200  # buckets of b = 100 keys stay far below 200
     assert p["split_evals"] <= p["split_evals_executed"] <= p["split_evals"] + 32 * max_m * p["split_nodes"]
     assert 5 * p["leaf_trials"] <= p["leaf_evals_executed"] <= 8 * (p["leaf_trials"] + 128 * p["leaf_nodes"])
