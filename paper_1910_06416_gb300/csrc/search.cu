@@ -102,10 +102,22 @@ struct SplitParams {
 // 7: F parts of equal size (m = F unit): the part is floor(F h / 2^32), one
 // multiply-high instead of two, counted in nbits-bit fields; when a field
 // can overflow (2^nbits <= m) a match is confirmed exactly as in mode 5.
+// 8..11: mode 7 with nbits = MODE - 3 (5..8) fixed at compile time.
 template <int MODE>
 __device__ __forceinline__ bool split_trial(const uint64_t* __restrict__ keys, const SplitParams& p,
                                             uint64_t kp) {
-  if (MODE == 6) {
+  if (MODE >= 8) {
+    // mode 7 with the field width fixed at compile time (5..8 bits): the
+    // field offset part * width is a shift-and-add on the ALU pipe instead of
+    // a multiply on the multiply-add pipe, which these nodes saturate (ncu,
+    // 560 -> 5 x 112 and 112 -> 7 x 16 at l = 16: multiply-add pipe 91% busy,
+    // ALU pipe 55%)
+    constexpr uint32_t NB = MODE - 3;
+    uint32_t acc = 0;
+#pragma unroll 4
+    for (uint32_t j = 0; j < p.m; j++) acc += shl32(1u, __umulhi(family_top32(keys[j], kp), p.fanout) * NB);
+    return (acc & p.nmask) == p.ntarget;
+  } else if (MODE == 6) {
     uint32_t acc = 0;
 #pragma unroll 4
     for (uint32_t j = 0; j < p.m; j++) acc += 1u << ((family_top32(keys[j], kp) >> 27) & 0x18u);
@@ -197,7 +209,7 @@ __device__ __forceinline__ void split_search_warp(const uint64_t* __restrict__ k
     }
     const uint64_t kp = family_key(base + lane, depth);
     bool ok = split_trial<MODE>(keys, sp, kp);
-    if ((MODE == 5 || (MODE == 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
+    if ((MODE == 5 || (MODE >= 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
     const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
     if (exec && lane == 0) *exec += 32 * sp.m;
     if (hits) {
@@ -261,7 +273,11 @@ __device__ void emit_children(const SearchArgs& a, const Node& nd, const uint64_
 }
 
 // Search parameters of a split node; returns the count mode (split_trial).
-__device__ __forceinline__ int split_setup(const Node& nd, const uint64_t* table, SplitParams& sp) {
+// fixed_width: modes 8..11 may be returned (only the shared-node kernel
+// instantiates them: in the one-group-per-node kernel four more search loops
+// made the register allocator spill).
+__device__ __forceinline__ int split_setup(const Node& nd, const uint64_t* table, SplitParams& sp,
+                                           bool fixed_width = false) {
   const uint64_t w1 = table[kTableWords * nd.m + 1];
   sp.m = nd.m;
   sp.unit = static_cast<uint32_t>(w1);
@@ -280,7 +296,7 @@ __device__ __forceinline__ int split_setup(const Node& nd, const uint64_t* table
   } else if (sp.fanout >= 5 && nd.m == sp.fanout * sp.unit && sp.unit >= 2 && nd.m < 65536) {
     const uint32_t nb = nd.m < 256 && fields * 8 <= 32 ? 8 : 32 - __clz(sp.unit);
     if (fields * nb <= 32) {
-      mode = 7;
+      mode = fixed_width && nb >= 5 && nb <= 8 ? static_cast<int>(nb) + 3 : 7;  // 8..11: the width at compile time
       sp.confirm = (1u << nb) <= nd.m;
       sp.nbits = nb;
       sp.nmask = fields * nb == 32 ? ~0u : (1u << (fields * nb)) - 1;
@@ -455,7 +471,7 @@ __device__ __forceinline__ uint32_t shared_search_warp(const uint64_t* __restric
       if (r && base >= volatile_load(best)) return rounds;
       const uint64_t kp = family_key(base + lane, depth);
       bool ok = split_trial<MODE>(keys, sp, kp);
-      if ((MODE == 5 || (MODE == 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
+      if ((MODE == 5 || (MODE >= 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
       const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
       rounds++;
       if (hits) {
@@ -477,6 +493,10 @@ __device__ __forceinline__ uint32_t shared_search(const uint64_t* __restrict__ k
     case 5: return shared_search_warp<5>(keys, sp, depth, lane, best, next, stall, limit, err);
     case 6: return shared_search_warp<6>(keys, sp, depth, lane, best, next, stall, limit, err);
     case 7: return shared_search_warp<7>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 8: return shared_search_warp<8>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 9: return shared_search_warp<9>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 10: return shared_search_warp<10>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 11: return shared_search_warp<11>(keys, sp, depth, lane, best, next, stall, limit, err);
     default: return shared_search_warp<2>(keys, sp, depth, lane, best, next, stall, limit, err);
   }
 }
@@ -574,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_shared(SearchArgs a, Shar
     __syncthreads();
     {
       SplitParams sp;
-      const int mode = split_setup(nd, table, sp);
+      const int mode = split_setup(nd, table, sp, /*fixed_width=*/true);
       const uint32_t rounds = shared_search(in_smem ? mine : src, sp, mode, depth, lane, &st.best[idx], &st.next[idx],
                                             stall_threshold(table, nd.m), trial_limit(table, nd.m), a.error);
       if (COUNT) evals += uint64_t(rounds) * 32 * nd.m;
