@@ -55,33 +55,46 @@ __device__ __forceinline__ void signature_u64(uint64_t key, uint64_t& hi, uint64
 // swapped, then the length folded into both.  The string is read with
 // aligned 4-byte loads of the words that hold at least one of its bytes (no
 // load leaves the page that holds the string); each 8-byte word is two funnel
-// shifts of three consecutive loaded words.  One loop covers every 8-byte
-// word including the zero-padded last one, so the lanes of a warp diverge
-// only by their number of words, not also by whether they have a tail.
+// shifts of three consecutive loaded words.  Every 8-byte word but the last
+// lies wholly inside the string, and so do the three 4-byte words it is cut
+// from (the last of them holds the word's byte 8, which the string has), so
+// those words are read without a bound or a mask; only the last 8-byte word
+// (1 to 8 bytes) checks which loads the string covers and masks its tail.
+__device__ __forceinline__ void absorb(uint64_t& a, uint64_t& c, uint64_t word) {
+  a = mix64(a ^ word);
+  c = mix64(c ^ ((word >> 32) | (word << 32)));
+}
+
 __device__ __forceinline__ void signature_bytes(const uint8_t* p, uint64_t len, uint64_t& hi, uint64_t& lo) {
   uint64_t a = kSigHi, c = kSigLo;
   if (len) {
     const uintptr_t addr = reinterpret_cast<uintptr_t>(p);
     const uint32_t* w = reinterpret_cast<const uint32_t*>(addr & ~uintptr_t(3));
     const uint32_t sh = static_cast<uint32_t>(addr & 3) * 8;
-    const uint64_t nt = ((addr + len - 1) >> 2) - (addr >> 2) + 1;  // words touched
-    const uint64_t nw = (len + 7) >> 3;
+    const uint64_t nt = ((addr + len - 1) >> 2) - (addr >> 2) + 1;  // 4-byte words touched
+    const uint64_t full = (len - 1) >> 3;                            // 8-byte words before the last
     uint32_t w0 = __ldg(w);
-    uint64_t j = 1;  // next word to load
-    // bytes 8i .. 8i + 7: words 2i (already loaded), 2i + 1 and 2i + 2, the
-    // last two only where they hold a byte of the string
-    for (uint64_t i = 0; i < nw; i++) {
-      const uint32_t w1 = j < nt ? __ldg(w + j) : 0u;
-      const uint32_t w2 = j + 1 < nt ? __ldg(w + j + 1) : 0u;
-      j += 2;
-      const uint64_t rem = len - 8 * i;
-      const uint32_t keep = rem < 8 ? static_cast<uint32_t>(rem) * 8 : 64u;  // bits of the word in the string
-      const uint64_t mask = ~0ull >> (64 - keep);
-      const uint64_t word = ((uint64_t(__funnelshift_r(w1, w2, sh)) << 32) | __funnelshift_r(w0, w1, sh)) & mask;
-      a = mix64(a ^ word);
-      c = mix64(c ^ ((word >> 32) | (word << 32)));
-      w0 = w2;
+    // 32-bit trip counts (the outer loop runs more than once only for strings
+    // of 32 GiB or more)
+    for (uint64_t left = full; left;) {
+      const uint32_t step = left < 0xFFFFFFFFull ? static_cast<uint32_t>(left) : 0xFFFFFFFFu;
+      left -= step;
+      for (uint32_t i = 0; i < step; i++) {
+        const uint32_t w1 = __ldg(w + 1), w2 = __ldg(w + 2);
+        w += 2;
+        absorb(a, c, (uint64_t(__funnelshift_r(w1, w2, sh)) << 32) | __funnelshift_r(w0, w1, sh));
+        w0 = w2;
+      }
     }
+    // the last 8-byte word: words 2 full + 1 and 2 full + 2 of the span,
+    // each only where it holds a byte of the string
+    const uint64_t j = 2 * full + 1;
+    const uint32_t w1 = j < nt ? __ldg(w + 1) : 0u;
+    const uint32_t w2 = j + 1 < nt ? __ldg(w + 2) : 0u;
+    const uint32_t keep = static_cast<uint32_t>(len - 8 * full) * 8;  // 8 .. 64 bits of the word in the string
+    const uint64_t word = ((uint64_t(__funnelshift_r(w1, w2, sh)) << 32) | __funnelshift_r(w0, w1, sh)) &
+                          (~0ull >> (64 - keep));
+    absorb(a, c, word);
   }
   hi = mix64(a + len);
   lo = mix64(c + len);
