@@ -155,15 +155,30 @@ def nvtx_pop():
         pass
 
 
+# headers every kernel source includes: a change there changes the kernels too
+KERNEL_HEADERS = ("device.cuh", "common.h")
+
+
+def kernel_source_sha(source, root=None):
+    """First 16 hex digits of the SHA-256 of a kernel source file followed by
+    the shared headers it includes (the hash an ncu summary records)."""
+    csrc = os.path.join(root or ROOT, "paper_1910_06416_gb300", "csrc")
+    h = hashlib.sha256(open(os.path.join(csrc, source), "rb").read())
+    for name in KERNEL_HEADERS:
+        path = os.path.join(csrc, name)
+        if os.path.exists(path):
+            h.update(open(path, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel_tag, source="search.cu", key="dram_bytes_per_launch"):
     """DRAM bytes recorded by an ncu capture summary (per launch, or with
     key="dram_bytes_all_launches" summed over the captured launches), if the
-    kernel source has not changed since (else None)."""
+    kernel source and its shared headers have not changed since (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_1910_06416_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha(source)
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
@@ -248,7 +263,18 @@ def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5, workers=0):
     half builds of log-uniform 10^4..10^7 byte-string keys (slices of the
     key pool), half lookups of log-uniform 10^3..10^6 member queries against
     a resident structure.  Latency is submission to completion."""
+    import torch
     rng = np.random.default_rng(seed)
+    # request payloads and results in pinned host memory, as a server's
+    # receive and reply buffers would be: their copies are then asynchronous
+    # DMA instead of the driver's staged copies of pageable memory
+    pin_data = torch.from_numpy(keys.data).pin_memory()
+    pin_offs = torch.from_numpy(keys.offsets.view(np.int64)).pin_memory()
+    data, offsets = pin_data.numpy(), pin_offs.numpy().view(np.uint64)
+    ring_cap = 1 << 25
+    pin_out = torch.empty(ring_cap, dtype=torch.int64, pin_memory=True)
+    ring = pin_out.numpy().view(np.uint64)
+    ring_pos = 0
     srv = rs.recsplit_server_create(hbm_budget_bytes=64 << 30, build_workers=workers)
     npool = keys.n
     times, t = [], 0.0
@@ -262,7 +288,7 @@ def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5, workers=0):
     qsize = np.floor(10 ** rng.uniform(3, 6, len(times))).astype(np.int64)
     pick = rng.random(len(times))
     resident = []  # (structure id, first key, keys)
-    info, outs, done = {}, {}, []
+    info, live, done = {}, {}, []  # live: lookup id -> its [start, end) of the result ring
 
     def drain(wait_ms=0):
         for c in rs.recsplit_server_poll(srv, 1024, wait_ms):
@@ -270,7 +296,18 @@ def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5, workers=0):
             kind, start, n = info[c["request_id"]]
             if kind == 0 and c["status"] == 0:
                 resident.append((c["structure_id"], start, n))
-            outs.pop(c["request_id"], None)
+            live.pop(c["request_id"], None)
+
+    def take(q):
+        """q result slots of the ring that no lookup in flight still writes."""
+        nonlocal ring_pos
+        if ring_pos + q > ring_cap:
+            ring_pos = 0
+        lo, hi = ring_pos, ring_pos + q
+        while any(a < hi and lo < b for a, b in live.values()):
+            drain(5)
+        ring_pos = hi
+        return lo, hi
 
     t0 = time.perf_counter()
     for i, te in enumerate(times):
@@ -282,14 +319,14 @@ def serve_run(rs, keys, seconds, rate, leaf, bucket, seed=5, workers=0):
             sid, start, n = resident[int(pick[i] * len(resident))]
             q = int(min(qsize[i], n))
             a0 = start + int(rng.integers(0, n - q + 1))
-            out = np.empty(q, dtype=np.uint64)
-            rid = rs.recsplit_server_submit_lookup_bytes(srv, sid, keys.data, keys.offsets[a0:a0 + q + 1], out)
+            lo, hi = take(q)
+            rid = rs.recsplit_server_submit_lookup_bytes(srv, sid, data, offsets[a0:a0 + q + 1], ring[lo:hi])
             info[rid] = (1, a0, q)
-            outs[rid] = out
+            live[rid] = (lo, hi)
         else:
             n = int(bsize[i])
             start = int(rng.integers(0, npool - n + 1))
-            rid = rs.recsplit_server_submit_build_bytes(srv, keys.data, keys.offsets[start:start + n + 1], leaf, bucket)
+            rid = rs.recsplit_server_submit_build_bytes(srv, data, offsets[start:start + n + 1], leaf, bucket)
             info[rid] = (0, start, n)
     while len(done) < len(info):
         drain(50)

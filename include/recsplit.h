@@ -238,7 +238,11 @@ uint64_t recsplit_launch_count(void);
  * request served alone.
  * Buffers passed to submit calls are host memory (the engine copies inputs
  * to the device when it starts the request) and must stay valid (inputs
- * unchanged, outputs untouched) until the request completes.
+ * unchanged, outputs untouched) until the request completes.  Pinned
+ * (page-locked) buffers are copied by asynchronous DMA; pageable ones go
+ * through the CUDA driver's staging, which is slower and can wait behind
+ * other staged copies, such as a large build's input.  The engine stages
+ * its own per-batch lookup arrays in pinned memory.
  * The paper has no serving layer; this is the interface of the library.
  * --------------------------------------------------------------------- */
 typedef struct recsplit_server recsplit_server_t;

@@ -288,5 +288,7 @@ int launch_leaves(const SearchArgs& a, uint32_t leaf, uint32_t extra, int sm_cou
 recsplit_tuning_t tuning_for(uint32_t leaf);
 void set_tuning_for(uint32_t leaf, const recsplit_tuning_t& t);
 recsplit_tuning_t default_tuning(uint32_t leaf);
+// Seeds per lane a leaf test mode starts from (one-phase: 1; phased: 4, 8 for large leaves).
+uint32_t natural_seeds_per_lane(uint32_t leaf, uint32_t two_phase);
 
 }  // namespace rs

@@ -719,6 +719,165 @@ __device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L],
   return win;
 }
 
+// Three-phase test for full leaves of L >= kFifoLeaf keys, with the
+// survivors of each phase kept, in index order, in first-in first-out
+// buffers of the warp that outlive the round: phase 1 maps the first h1 keys
+// of the round's spl * 32 indices and appends the survivors to A; phase 2
+// maps keys h1 .. h2 - 1 of 32 entries of A at a time and appends its
+// survivors to B; phase 3 finishes 32 entries of B at a time.  A batch runs
+// only once its buffer holds 32 entries, so every phase works on full
+// warps (the two-phase round above finishes its few survivors, about 0.12 of
+// 32 * spl at l = 16, in a mostly idle batch every round).  Entries leave
+// each buffer in the order they entered it and every entry of B is older
+// than every entry of A, so the first index that phase 3 completes is the
+// smallest bijective index among all the indices the warp has generated.
+// When the warp stops (another warp of its group found a smaller index, or
+// the trial limit) it first drains both buffers with partial batches.
+//
+// h1 < h2 minimise the expected work per index, h1 + P_h1 (h2 - h1 + c) +
+// P_h2 (l - h2 + c) evaluations with c = 2.5 for the compaction and reload of
+// a survivor (P_h as above): (6, 8) at l = 12, (7, 10) at 16, (8, 13) at 24.
+struct LeafPhases {
+  int h1, h2;
+};
+__host__ __device__ constexpr LeafPhases leaf_phases(int l) {
+  double best = 1e30;
+  LeafPhases arg{1, 2};
+  double p1 = 1.0;  // P_h1
+  for (int h1 = 1; h1 < l - 1; h1++) {
+    double p2 = p1;  // P_h2
+    for (int h2 = h1 + 1; h2 < l; h2++) {
+      p2 = p2 * (l - (h2 - 1)) / l;
+      const double cost = h1 + p1 * (h2 - h1 + 2.5) + p2 * (l - h2 + 2.5);
+      if (cost < best) {
+        best = cost;
+        arg = LeafPhases{h1, h2};
+      }
+    }
+    p1 = p1 * (l - h1) / l;
+  }
+  return arg;
+}
+constexpr int kFifoLeaf = 12;
+constexpr uint32_t kFifoA = 32 * kMaxSpl + 32;  // below 32 left + one round's spl * 32
+constexpr uint32_t kFifoB = 64;                 // below 32 left + one batch of A
+// Entries carry the low 32 bits of their index; the buffers are drained
+// every 2^16 rounds, so an entry is less than 2^16 * 16 * 32 * kMaxSpl < 2^32
+// indices older than the newest and its index is recovered exactly.
+constexpr uint32_t kFifoDrainRounds = 1u << 16;
+
+// Moves entries [r, n) of a warp buffer, fewer than 32, to its front.
+__device__ __forceinline__ uint32_t fifo_compact(uint4* buf, uint32_t r, uint32_t n, uint32_t lane) {
+  const uint32_t rem = n - r;
+  uint4 v = make_uint4(0, 0, 0, 0);
+  if (lane < rem) v = buf[r + lane];
+  __syncwarp();
+  if (lane < rem) buf[lane] = v;
+  __syncwarp();
+  return rem;
+}
+
+template <int L>
+__device__ __forceinline__ void fifo_phase1(const uint64_t (&x)[L], uint64_t base, uint64_t dkey, uint32_t spl,
+                                            uint32_t lane, uint4* a, uint32_t& na) {
+  constexpr int H1 = leaf_phases(L).h1;
+  const uint32_t below = (1u << lane) - 1;
+  uint64_t k = index_key(base + lane, dkey);
+  for (uint32_t j = 0; j < spl; j++, k += kLaneStep) {
+    const uint64_t kp = k ^ (k >> 30);
+    uint32_t seen = 0;
+#pragma unroll
+    for (int i = 0; i < H1; i++) seen += 1u << phi_fixed<L>(x[i], kp);
+    const bool ok = __popc(seen) == H1;
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok)
+      a[na + __popc(b & below)] = make_uint4(static_cast<uint32_t>(base) + j * 32 + lane, seen,
+                                             static_cast<uint32_t>(kp), static_cast<uint32_t>(kp >> 32));
+    na += __popc(b);
+  }
+  __syncwarp();
+}
+
+// Phase 2 on entries [ra, ra + c) of A (c <= 32); survivors go to B.
+template <int L>
+__device__ __forceinline__ void fifo_phase2(const uint64_t (&x)[L], const uint4* a, uint32_t ra, uint32_t c,
+                                            uint32_t lane, uint4* b, uint32_t& nb) {
+  constexpr LeafPhases ph = leaf_phases(L);
+  uint4 e = make_uint4(0, 0, 0, 0);
+  bool ok = false;
+  if (lane < c) {
+    e = a[ra + lane];
+    const uint64_t kp = (uint64_t(e.w) << 32) | e.z;
+#pragma unroll
+    for (int i = ph.h1; i < ph.h2; i++) e.y += 1u << phi_fixed<L>(x[i], kp);
+    ok = __popc(e.y) == ph.h2;
+  }
+  const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+  if (ok) b[nb + __popc(hits & ((1u << lane) - 1))] = e;
+  nb += __popc(hits);
+  __syncwarp();
+}
+
+// Phase 3 on entries [rb, rb + c) of B; on success `low` is the low 32 bits
+// of the first bijective entry's index.
+template <int L>
+__device__ __forceinline__ bool fifo_phase3(const uint64_t (&x)[L], const uint4* b, uint32_t rb, uint32_t c,
+                                            uint32_t lane, uint32_t& low) {
+  constexpr int H2 = leaf_phases(L).h2;
+  constexpr uint32_t full = L == 32 ? ~0u : ((1u << L) - 1);
+  bool ok = false;
+  uint32_t id = 0;
+  if (lane < c) {
+    const uint4 e = b[rb + lane];
+    const uint64_t kp = (uint64_t(e.w) << 32) | e.z;
+    uint32_t seen = e.y;
+#pragma unroll
+    for (int i = H2; i < L; i++) seen += 1u << phi_fixed<L>(x[i], kp);
+    ok = seen == full;
+    id = e.x;
+  }
+  const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+  if (!hits) return false;
+  low = __shfl_sync(0xFFFFFFFFu, id, __ffs(hits) - 1);
+  return true;
+}
+
+// Phases 2 and 3 on the full batches of the warp's buffers (on every entry
+// with `drain`).  `newest` is the largest index generated so far.  Returns
+// the smallest bijective index found, or ~0.
+template <int L>
+__device__ __forceinline__ uint64_t fifo_pump(const uint64_t (&x)[L], uint4* a, uint32_t& na, uint4* b, uint32_t& nb,
+                                              bool drain, uint64_t newest, uint32_t lane,
+                                              unsigned long long* exec) {
+  constexpr LeafPhases ph = leaf_phases(L);
+  uint32_t ra = 0, low = 0;
+  bool found = false;
+  while (!found && (na - ra >= 32 || (drain && na > ra))) {
+    const uint32_t c = min(32u, na - ra);
+    fifo_phase2<L>(x, a, ra, c, lane, b, nb);
+    if (exec && lane == 0) *exec += c * (ph.h2 - ph.h1);
+    ra += c;
+    uint32_t rb = 0;
+    while (nb - rb >= 32) {
+      if (exec && lane == 0) *exec += 32 * (L - ph.h2);
+      if ((found = fifo_phase3<L>(x, b, rb, 32, lane, low))) break;
+      rb += 32;
+    }
+    if (!found) nb = fifo_compact(b, rb, nb, lane);
+  }
+  if (!found) {
+    na = fifo_compact(a, ra, na, lane);  // fewer than 32 left unless draining, which leaves none
+    for (uint32_t rb = 0; drain && rb < nb; rb += 32) {
+      const uint32_t c = min(32u, nb - rb);
+      if (exec && lane == 0) *exec += c * (L - ph.h2);
+      if ((found = fifo_phase3<L>(x, b, rb, c, lane, low))) break;
+    }
+    if (drain) nb = 0;
+  }
+  if (!found) return ~0ull;
+  return newest - static_cast<uint32_t>(static_cast<uint32_t>(newest) - low);
+}
+
 // Leaf of m < LMAX keys: slots j >= m contribute nothing.
 template <int LMAX>
 __device__ __forceinline__ bool leaf_trial_part(const uint64_t (&x)[LMAX], const uint32_t (&keep)[LMAX], uint32_t m,
@@ -755,7 +914,9 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
   __shared__ uint32_t task[kWarps];
   __shared__ unsigned long long wexec[kWarps];  // work counting: evaluations per warp, flushed at exit
   constexpr bool kTwoPhase = FULL && TWO && LMAX >= 4;
-  __shared__ uint4 surv[kTwoPhase ? kWarps : 1][kTwoPhase ? 32 * kMaxSpl : 1];
+  constexpr bool kFifo = kTwoPhase && LMAX >= kFifoLeaf;
+  // two-phase rounds: one round's survivors; three phases: buffers A and B
+  __shared__ uint4 surv[kTwoPhase ? kWarps : 1][kFifo ? kFifoA + kFifoB : (kTwoPhase ? 32 * kMaxSpl : 1)];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned long long* const exec = a.exec_count ? &wexec[warp] : nullptr;
   if (lane == 0) wexec[warp] = 0;
@@ -795,6 +956,55 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
       // a round of a warp covers the spl * 32 indices from base; lane L tests
       // base + j * 32 + L for j < spl
       const uint64_t span = uint64_t(spl) * 32;
+      if constexpr (kFifo) {
+        uint4* const fa = surv[warp];
+        uint4* const fb = surv[warp] + kFifoA;
+        uint32_t na = 0, nb = 0;
+        uint64_t newest = 0;
+        for (uint64_t base = uint64_t(wig) * span;; base += uint64_t(gwarps) * span) {
+          bool drain = false, last = false, at_limit = false;
+          if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(&best[gid]))) {
+            drain = last = true;  // another warp found a smaller index than this one's next
+          } else if ((++rounds & 255) == 0 &&
+                     __shfl_sync(0xFFFFFFFFu, lane == 0 ? *reinterpret_cast<volatile int*>(a.error) : 0, 0)) {
+            break;  // another search failed, or the host cancelled the build
+          } else if (base >= limit) {
+            drain = last = at_limit = true;  // an index below the limit may still wait in the buffers
+          } else {
+            if (!checked && base >= stall) {
+              checked = true;
+              bool dup = false;
+#pragma unroll
+              for (int i = 0; i < LMAX; i++)
+#pragma unroll
+                for (int j = i + 1; j < LMAX; j++) dup |= x[i] == x[j];
+              if (dup) {
+                if (lane == 0) {
+                  set_error(a.error, RECSPLIT_E_DUPLICATE);
+                  atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), 0ull);
+                }
+                break;
+              }
+            }
+            fifo_phase1<LMAX>(x, base, dkey, spl, lane, fa, na);
+            if (exec && lane == 0) *exec += spl * 32 * leaf_phases(LMAX).h1;
+            newest = base + span - 1;
+            drain = (rounds % kFifoDrainRounds) == 0;
+          }
+          const uint64_t found = na || nb ? fifo_pump<LMAX>(x, fa, na, fb, nb, drain, newest, lane, exec) : ~0ull;
+          if (found != ~0ull) {
+            if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), found);
+            break;
+          }
+          if (last) {
+            if (at_limit && lane == 0) {
+              set_error(a.error, RECSPLIT_E_SEARCH_LIMIT);
+              atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), 0ull);
+            }
+            break;
+          }
+        }
+      } else
       for (uint64_t base = uint64_t(wig) * span;; base += uint64_t(gwarps) * span) {
         if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(&best[gid]))) break;
         if ((++rounds & 255) == 0 &&
@@ -925,12 +1135,21 @@ recsplit_tuning_t g_tune[kMaxLeaf + 1];
 bool g_tuned[kMaxLeaf + 1] = {};
 }  // namespace
 
+// Seeds per lane that a leaf test mode starts from: one for the one-phase
+// test; for the phased tests four, and the most, eight, from kFifoLeaf keys
+// on, where survivors wait in the buffers across rounds and longer rounds
+// only spread the per-round checks over more indices.
+uint32_t natural_seeds_per_lane(uint32_t leaf, uint32_t two_phase) {
+  if (!two_phase) return 1;
+  return leaf >= static_cast<uint32_t>(kFifoLeaf) ? kMaxSpl : 4;
+}
+
 recsplit_tuning_t default_tuning(uint32_t leaf) {
   recsplit_tuning_t t;
   t.leaf_warps = leaf >= 12 ? 4 : 1;
   t.leaf_chunk = leaf >= 12 ? 1 : 4;
   t.leaf_two_phase = leaf >= 10 ? 1 : 0;
-  t.leaf_seeds_per_lane = t.leaf_two_phase ? 4 : 1;
+  t.leaf_seeds_per_lane = natural_seeds_per_lane(leaf, t.leaf_two_phase);
   t.split_warps[0] = 1;
   t.split_warps[1] = leaf >= 12 ? 2 : 1;
   t.split_warps[2] = 8;

@@ -94,6 +94,34 @@ struct Server {
   std::thread tl;
   std::vector<cudaStream_t> sb_small, sb_large;  // per build worker
   cudaStream_t sl = nullptr;
+  // The lookup worker's staging of request ids and rebased offsets: pinned,
+  // so that their copies are asynchronous DMA and do not queue behind the
+  // driver's staged copies of pageable buffers (a large build's input, for
+  // instance); pageable memory when pinned memory cannot be had.
+  void* pin = nullptr;
+  uint64_t pin_bytes = 0;
+  std::vector<uint64_t> unpinned;
+
+  // At least `bytes` of staging, 8-byte aligned.  Called between batches,
+  // after the previous batch's copies have completed.
+  uint8_t* staging(uint64_t bytes) {
+    if (bytes > pin_bytes) {
+      if (pin) cudaFreeHost(pin);
+      pin = nullptr;
+      pin_bytes = 0;
+      uint64_t want = 16ull << 20;
+      while (want < bytes) want *= 2;
+      if (cudaHostAlloc(&pin, want, cudaHostAllocDefault) == cudaSuccess) {
+        pin_bytes = want;
+      } else {
+        cudaGetLastError();  // clear the failed allocation and stage in pageable memory
+        pin = nullptr;
+      }
+    }
+    if (bytes <= pin_bytes) return static_cast<uint8_t*>(pin);
+    unpinned.resize((bytes + 7) / 8);
+    return reinterpret_cast<uint8_t*>(unpinned.data());
+  }
 
   void complete(const Req& r, int status, uint64_t items, uint32_t batch) {
     recsplit_completion_t c{};
@@ -277,13 +305,19 @@ struct Server {
           if (kind == 1 && r.n) nbytes += r.offsets[r.n] - r.offsets[0];
         }
       if (!q) continue;
-      std::vector<uint32_t> ids(q);
-      std::vector<uint64_t> offs(kind == 1 ? q + 1 : 0);
+      // offsets (8-byte aligned), the views, then the ids
+      const uint64_t off_bytes = kind == 1 ? (q + 1) * 8 : 0, view_bytes = views.size() * sizeof(View);
+      static_assert(sizeof(View) % 8 == 0, "views keep the ids 8-byte aligned");
+      uint8_t* const stage = staging(off_bytes + view_bytes + q * 4);
+      uint64_t* const offs = reinterpret_cast<uint64_t*>(stage);
+      View* const vstage = reinterpret_cast<View*>(stage + off_bytes);
+      uint32_t* const ids = reinterpret_cast<uint32_t*>(stage + off_bytes + view_bytes);
+      std::copy(views.begin(), views.end(), vstage);
       uint64_t pos = 0, bpos = 0;
       for (size_t i = 0; i < batch.size(); i++) {
         const Req& r = batch[i];
         if ((r.u64 != nullptr) != (kind == 0)) continue;
-        std::fill(ids.begin() + pos, ids.begin() + pos + r.n, static_cast<uint32_t>(view_of[i]));
+        std::fill(ids + pos, ids + pos + r.n, static_cast<uint32_t>(view_of[i]));
         if (kind == 1) {
           for (uint64_t j = 0; j < r.n; j++) offs[pos + j] = bpos + (r.offsets[j] - r.offsets[0]);
           bpos += r.n ? r.offsets[r.n] - r.offsets[0] : 0;
@@ -304,8 +338,8 @@ struct Server {
         for (void* p : staged) cudaFreeAsync(p, sl);
         break;
       }
-      cudaMemcpyAsync(d_views, views.data(), views.size() * sizeof(View), cudaMemcpyHostToDevice, sl);
-      cudaMemcpyAsync(d_ids, ids.data(), q * 4, cudaMemcpyHostToDevice, sl);
+      cudaMemcpyAsync(d_views, vstage, view_bytes, cudaMemcpyHostToDevice, sl);
+      cudaMemcpyAsync(d_ids, ids, q * 4, cudaMemcpyHostToDevice, sl);
       pos = 0;
       bpos = 0;
       for (const Req& r : batch) {
@@ -319,7 +353,7 @@ struct Server {
         }
         pos += r.n;
       }
-      if (kind == 1) cudaMemcpyAsync(d_offs, offs.data(), (q + 1) * 8, cudaMemcpyHostToDevice, sl);
+      if (kind == 1) cudaMemcpyAsync(d_offs, offs, (q + 1) * 8, cudaMemcpyHostToDevice, sl);
       const uint32_t nviews = static_cast<uint32_t>(views.size());
       rc = kind == 0 ? lookup_many(static_cast<View*>(d_views), nviews, static_cast<uint32_t*>(d_ids),
                                    static_cast<uint64_t*>(d_keys), q, static_cast<uint64_t*>(d_out), sl,
@@ -400,6 +434,7 @@ void recsplit_server_destroy(recsplit_server_t* sp) {
   for (cudaStream_t x : s->sb_small) cudaStreamDestroy(x);
   for (cudaStream_t x : s->sb_large) cudaStreamDestroy(x);
   cudaStreamDestroy(s->sl);
+  if (s->pin) cudaFreeHost(s->pin);
   delete s;
 }
 

@@ -111,7 +111,7 @@ int recsplit_autotune(uint32_t leaf_size, uint32_t bucket_size, uint64_t sample_
     for (uint32_t tp : {0u, 1u}) {
       recsplit_tuning_t t = best;
       t.leaf_two_phase = tp;
-      t.leaf_seeds_per_lane = tp ? 4 : 1;
+      t.leaf_seeds_per_lane = natural_seeds_per_lane(leaf_size, tp);
       double ms;
       if ((rc = measure(t, true, &ms))) break;
       if (better(ms, leaf_ms)) leaf_ms = ms, best = t;

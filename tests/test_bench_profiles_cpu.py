@@ -1,6 +1,7 @@
 """bench.py reads DRAM traffic and utilisation counters from the ncu summaries
-under profiles/ only while the kernel source they were captured from is
-unchanged (its hash is recorded in the summary)."""
+under profiles/ only while the kernel source they were captured from, and the
+shared headers it includes, are unchanged (their hash is recorded in the
+summary)."""
 import hashlib
 import os
 import sys
@@ -24,18 +25,30 @@ SUMMARY = """# test kernel
 """
 
 
+HEADER = "__device__ int f() { return 1; }\n"
+
+
 def make_tree(tmp_path, source_text, recorded_sha):
     csrc = tmp_path / "paper_1910_06416_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (csrc / "k.cu").write_text(source_text)
+    (csrc / "device.cuh").write_text(HEADER)
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "k_test.md").write_text(SUMMARY.format(sha=recorded_sha))
+    return csrc
+
+
+def sha_of(*texts):
+    h = hashlib.sha256()
+    for t in texts:
+        h.update(t.encode())
+    return h.hexdigest()[:16]
 
 
 def test_counters_are_read_while_the_source_is_unchanged(tmp_path, monkeypatch):
     src = "__global__ void k() {}\n"
-    make_tree(tmp_path, src, hashlib.sha256(src.encode()).hexdigest()[:16])
+    make_tree(tmp_path, src, sha_of(src, HEADER))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_from_profiles("k_test", "k.cu") == 1234.0
     assert bench.traffic_from_profiles("k_test", "k.cu", key="dram_bytes_all_launches") == 5678.0
@@ -48,3 +61,12 @@ def test_counters_are_dropped_once_the_source_changes(tmp_path, monkeypatch):
     assert bench.traffic_from_profiles("k_test", "k.cu") is None
     assert bench.counters_from_profiles("k_test", "k.cu") is None
     assert bench.traffic_from_profiles("missing", "k.cu") is None
+
+
+def test_counters_are_dropped_once_a_shared_header_changes(tmp_path, monkeypatch):
+    src = "__global__ void k() {}\n"
+    csrc = make_tree(tmp_path, src, sha_of(src, HEADER))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("k_test", "k.cu") == 1234.0
+    (csrc / "device.cuh").write_text(HEADER + "// changed\n")
+    assert bench.traffic_from_profiles("k_test", "k.cu") is None
