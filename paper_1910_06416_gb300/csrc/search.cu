@@ -88,6 +88,7 @@ struct SplitParams {
   uint32_t cum_target;      // sum over k of k * unit << ((k - 1) * B)
   uint32_t nbits, nmask, ntarget;  // narrow fields (modes 5, 7): 2^nbits > unit
   bool confirm;                    // mode 7: fields can overflow, confirm matches exactly
+  uint32_t tail;                   // modes 8..11 on shared nodes: keys of the second phase (0: one phase)
 };
 
 // MODE 0: 32-bit fields + magic; 1: 64-bit fields + magic; 2: 64-bit +
@@ -279,6 +280,7 @@ __device__ void emit_children(const SearchArgs& a, const Node& nd, const uint64_
 __device__ __forceinline__ int split_setup(const Node& nd, const uint64_t* table, SplitParams& sp,
                                            bool fixed_width = false) {
   const uint64_t w1 = table[kTableWords * nd.m + 1];
+  sp.tail = 0;
   sp.m = nd.m;
   sp.unit = static_cast<uint32_t>(w1);
   sp.fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
@@ -297,6 +299,10 @@ __device__ __forceinline__ int split_setup(const Node& nd, const uint64_t* table
     const uint32_t nb = nd.m < 256 && fields * 8 <= 32 ? 8 : 32 - __clz(sp.unit);
     if (fields * nb <= 32) {
       mode = fixed_width && nb >= 5 && nb <= 8 ? static_cast<int>(nb) + 3 : 7;  // 8..11: the width at compile time
+      // second-phase keys of the two-phase block search (speed only: any
+      // value from 1 to m - 1 gives the same index); about 1.75 sqrt(m)
+      // minimises the modelled work: 19 of 112 keys, 18 of 96, 42 of 560
+      if (mode >= 8) sp.tail = min(nd.m - 1, static_cast<uint32_t>(1.75f * sqrtf(static_cast<float>(nd.m))) + 1);
       sp.confirm = (1u << nb) <= nd.m;
       sp.nbits = nb;
       sp.nmask = fields * nb == 32 ? ~0u : (1u << (fields * nb)) - 1;
@@ -436,25 +442,101 @@ constexpr uint32_t kShareRounds = 4;
 constexpr uint32_t kNodeOpen = 1, kNodeClosed = 2;
 constexpr uint32_t kMaxJoins = 4096;  // nodes one CTA may join in one launch
 
-// Returns the number of rounds of 32 indices the warp evaluated.
+// Fixed-width fields (modes 8..11) of keys [j0, j1) under function kp.
+template <int NB>
+__device__ __forceinline__ uint32_t split_fields(const uint64_t* __restrict__ keys, const SplitParams& p, uint64_t kp,
+                                                 uint32_t j0, uint32_t j1) {
+  uint32_t acc = 0;
+#pragma unroll 4
+  for (uint32_t j = j0; j < j1; j++) acc += shl32(1u, __umulhi(family_top32(keys[j], kp), p.fanout) * NB);
+  return acc;
+}
+
+// Two-phase test of one claimed block (kShareRounds * 32 indices from base0)
+// for the equal-part modes 8..11: phase 1 counts the first m - tail keys of
+// every index and keeps, in index order, those whose parts all still hold at
+// most unit keys; phase 2 adds the last tail keys of the survivors, 32 at a
+// time, and applies the one-phase test to the sum (the same fields: the
+// accumulation is a sum).  An index dropped in phase 1 has a part with more
+// than unit keys, so the one-phase test (after its exact confirmation) would
+// reject it too: the smallest successful index of the block is unchanged.
+// While every part holds at most unit < 2^NB keys no field overflows, so the
+// fields read in phase 1 are exact for the indices that are kept; an index
+// whose fields overflowed has a part beyond unit and may be kept or dropped.
+// Returns the evaluations executed; `hit` the smallest successful index, if any.
 template <int MODE>
-__device__ __forceinline__ uint32_t shared_search_warp(const uint64_t* __restrict__ keys, const SplitParams& sp,
+__device__ __forceinline__ uint64_t shared_block_two_phase(const uint64_t* __restrict__ keys, const SplitParams& sp,
+                                                           uint32_t depth, uint32_t lane, uint64_t base0,
+                                                           uint64_t* best, uint4* surv, uint64_t* hit) {
+  constexpr uint32_t NB = MODE - 3;
+  const uint32_t head = sp.m - sp.tail, fmask = (1u << NB) - 1;
+  const uint32_t below = (1u << lane) - 1;
+  uint64_t evals = 0;
+  uint32_t ns = 0;
+  for (uint32_t r = 0; r < kShareRounds; r++) {
+    const uint64_t base = base0 + r * 32;
+    if (r && base >= volatile_load(best)) break;  // a smaller index is known: the rest cannot win
+    const uint64_t kp = family_key(base + lane, depth);
+    const uint32_t acc = split_fields<NB>(keys, sp, kp, 0, head);
+    uint32_t counted = 0;
+    bool keep = true;
+    for (uint32_t t = 0; t + 1 < sp.fanout; t++) {
+      const uint32_t f = (acc >> (t * NB)) & fmask;
+      keep &= f <= sp.unit;
+      counted += f;
+    }
+    keep &= counted <= head && head - counted <= sp.unit;  // the last part
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+    if (keep)
+      surv[ns + __popc(b & below)] =
+          make_uint4(r * 32 + lane, acc, static_cast<uint32_t>(kp), static_cast<uint32_t>(kp >> 32));
+    ns += __popc(b);
+    evals += 32 * head;
+  }
+  __syncwarp();
+  *hit = ~0ull;
+  for (uint32_t t0 = 0; t0 < ns; t0 += 32) {
+    const uint32_t t = t0 + lane;
+    bool ok = false;
+    if (t < ns) {
+      const uint4 e = surv[t];
+      const uint64_t kp = (uint64_t(e.w) << 32) | e.z;
+      const uint32_t acc = e.y + split_fields<NB>(keys, sp, kp, head, sp.m);
+      ok = (acc & sp.nmask) == sp.ntarget;
+      if (ok && sp.confirm) ok = split_trial<1>(keys, sp, kp);
+    }
+    evals += uint64_t(min(32u, ns - t0)) * sp.tail;
+    const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
+    if (hits) {
+      *hit = base0 + surv[t0 + __ffs(hits) - 1].x;
+      break;
+    }
+  }
+  __syncwarp();
+  return evals;
+}
+
+// Returns the evaluations the warp executed (32 * m per round of 32 indices,
+// or as counted by the two-phase block test).
+template <int MODE>
+__device__ __forceinline__ uint64_t shared_search_warp(const uint64_t* __restrict__ keys, const SplitParams& sp,
                                                        uint32_t depth, uint32_t lane, uint64_t* best,
                                                        unsigned int* next, uint64_t stall, uint64_t limit,
-                                                       int* err) {
-  uint32_t blocks = 0, rounds = 0;
+                                                       int* err, uint4* surv) {
+  uint32_t blocks = 0;
+  uint64_t evals = 0;
   for (;;) {
     uint32_t blk = 0;
     if (lane == 0) blk = atomicAdd(next, 1u);
     const uint64_t base0 = uint64_t(__shfl_sync(0xFFFFFFFFu, blk, 0)) * (kShareRounds * 32);
-    if (base0 >= volatile_load(best)) return rounds;
+    if (base0 >= volatile_load(best)) return evals;
     if ((++blocks & 63) == 0 && __shfl_sync(0xFFFFFFFFu, lane == 0 ? *reinterpret_cast<volatile int*>(err) : 0, 0))
-      return rounds;  // another search failed, or the host cancelled the build
+      return evals;  // another search failed, or the host cancelled the build
     // Blocks at or beyond the limit are not searched.  Participants claim
     // ahead of the frontier, so a claim there does not mean the search
     // failed: the node's closer reports the limit if no index below it
     // succeeded (every block below it was then claimed and tested).
-    if (base0 >= limit) return rounds;
+    if (base0 >= limit) return evals;
     // the one warp whose block holds the stall point checks for keys that
     // can never be separated (an O(m^2) scan, done once per node)
     if (base0 <= stall && stall < base0 + kShareRounds * 32) {
@@ -463,41 +545,50 @@ __device__ __forceinline__ uint32_t shared_search_warp(const uint64_t* __restric
           set_error(err, RECSPLIT_E_DUPLICATE);
           atomicMin(reinterpret_cast<unsigned long long*>(best), 0ull);
         }
-        return rounds;
+        return evals;
       }
+    }
+    if (MODE >= 8 && sp.tail) {
+      uint64_t hit;
+      evals += shared_block_two_phase<MODE >= 8 ? MODE : 8>(keys, sp, depth, lane, base0, best, surv, &hit);
+      if (hit != ~0ull) {
+        if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(best), hit);
+        return evals;
+      }
+      continue;
     }
     for (uint32_t r = 0; r < kShareRounds; r++) {
       const uint64_t base = base0 + r * 32;
-      if (r && base >= volatile_load(best)) return rounds;
+      if (r && base >= volatile_load(best)) return evals;
       const uint64_t kp = family_key(base + lane, depth);
       bool ok = split_trial<MODE>(keys, sp, kp);
       if ((MODE == 5 || (MODE >= 7 && sp.confirm)) && ok) ok = split_trial<1>(keys, sp, kp);
       const uint32_t hits = __ballot_sync(0xFFFFFFFFu, ok);
-      rounds++;
+      evals += 32 * sp.m;
       if (hits) {
         if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(best), base + __ffs(hits) - 1);
-        return rounds;
+        return evals;
       }
     }
   }
 }
 
-__device__ __forceinline__ uint32_t shared_search(const uint64_t* __restrict__ keys, const SplitParams& sp, int mode,
+__device__ __forceinline__ uint64_t shared_search(const uint64_t* __restrict__ keys, const SplitParams& sp, int mode,
                                                   uint32_t depth, uint32_t lane, uint64_t* best, unsigned int* next,
-                                                  uint64_t stall, uint64_t limit, int* err) {
+                                                  uint64_t stall, uint64_t limit, int* err, uint4* surv) {
   switch (mode) {
-    case 0: return shared_search_warp<0>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 1: return shared_search_warp<1>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 3: return shared_search_warp<3>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 4: return shared_search_warp<4>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 5: return shared_search_warp<5>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 6: return shared_search_warp<6>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 7: return shared_search_warp<7>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 8: return shared_search_warp<8>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 9: return shared_search_warp<9>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 10: return shared_search_warp<10>(keys, sp, depth, lane, best, next, stall, limit, err);
-    case 11: return shared_search_warp<11>(keys, sp, depth, lane, best, next, stall, limit, err);
-    default: return shared_search_warp<2>(keys, sp, depth, lane, best, next, stall, limit, err);
+    case 0: return shared_search_warp<0>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 1: return shared_search_warp<1>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 3: return shared_search_warp<3>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 4: return shared_search_warp<4>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 5: return shared_search_warp<5>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 6: return shared_search_warp<6>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 7: return shared_search_warp<7>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 8: return shared_search_warp<8>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 9: return shared_search_warp<9>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 10: return shared_search_warp<10>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    case 11: return shared_search_warp<11>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
+    default: return shared_search_warp<2>(keys, sp, depth, lane, best, next, stall, limit, err, surv);
   }
 }
 
@@ -510,6 +601,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_shared(SearchArgs a, Shar
   extern __shared__ uint64_t mine[];
   __shared__ uint32_t task, owner, closer, drained;
   __shared__ uint32_t fill[16];
+  __shared__ uint4 surv[kWarps][kShareRounds * 32];  // two-phase block survivors, per warp
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t total = *a.split_in_count;
   volatile uint32_t* vflag = st.flag;
@@ -595,9 +687,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_split_shared(SearchArgs a, Shar
     {
       SplitParams sp;
       const int mode = split_setup(nd, table, sp, /*fixed_width=*/true);
-      const uint32_t rounds = shared_search(in_smem ? mine : src, sp, mode, depth, lane, &st.best[idx], &st.next[idx],
-                                            stall_threshold(table, nd.m), trial_limit(table, nd.m), a.error);
-      if (COUNT) evals += uint64_t(rounds) * 32 * nd.m;
+      const uint64_t done = shared_search(in_smem ? mine : src, sp, mode, depth, lane, &st.best[idx], &st.next[idx],
+                                          stall_threshold(table, nd.m), trial_limit(table, nd.m), a.error, surv[warp]);
+      if (COUNT) evals += done;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -736,7 +828,11 @@ __device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L],
 //
 // h1 < h2 minimise the expected work per index, h1 + P_h1 (h2 - h1 + c) +
 // P_h2 (l - h2 + c) evaluations with c = 2.5 for the compaction and reload of
-// a survivor (P_h as above): (6, 8) at l = 12, (7, 10) at 16, (8, 13) at 24.
+// a survivor (P_h as above): (6, 9) at l = 13, (7, 10) at 16, (8, 13) at 24.
+// At l = 12 a leaf takes about 2 * 10^4 trials, a few rounds of a group, and
+// draining the buffers at the end of every leaf costs more than the full
+// batches save (measured: 6% slower than the two-phase round), so the
+// buffers start at 13 keys.
 struct LeafPhases {
   int h1, h2;
 };
@@ -758,7 +854,7 @@ __host__ __device__ constexpr LeafPhases leaf_phases(int l) {
   }
   return arg;
 }
-constexpr int kFifoLeaf = 12;
+constexpr int kFifoLeaf = 13;
 constexpr uint32_t kFifoA = 32 * kMaxSpl + 32;  // below 32 left + one round's spl * 32
 constexpr uint32_t kFifoB = 64;                 // below 32 left + one batch of A
 // Entries carry the low 32 bits of their index; the buffers are drained
@@ -1136,12 +1232,13 @@ bool g_tuned[kMaxLeaf + 1] = {};
 }  // namespace
 
 // Seeds per lane that a leaf test mode starts from: one for the one-phase
-// test; for the phased tests four, and the most, eight, from kFifoLeaf keys
-// on, where survivors wait in the buffers across rounds and longer rounds
-// only spread the per-round checks over more indices.
+// test; for the phased tests four, and the most, eight, from 12 keys on,
+// where a leaf takes thousands of trials and longer rounds spread the
+// per-round checks over more indices (measured faster at l = 12 to 16 with
+// either phased test).
 uint32_t natural_seeds_per_lane(uint32_t leaf, uint32_t two_phase) {
   if (!two_phase) return 1;
-  return leaf >= static_cast<uint32_t>(kFifoLeaf) ? kMaxSpl : 4;
+  return leaf >= 12 ? kMaxSpl : 4;
 }
 
 recsplit_tuning_t default_tuning(uint32_t leaf) {
