@@ -628,13 +628,23 @@ def space_optimal_entry(rs, dev, stream, steps=2, warmup=1, queries=10_000_000):
             for k in ("ms_signature", "ms_group", "ms_split", "ms_leaf", "ms_encode", "ms_total")}
     peak_ops = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
     build_ms = statistics.median(bt)
+    rooflines = search_rooflines(prof, work, peak_ops)
+    # DRAM traffic and utilisation of the dominant launches, from their ncu
+    # summaries (the full-leaf launch; the two levels on shared nodes)
+    tag = f"u64_n{n}_l{leaf}_b{b}"
+    for name, summary, key, scope in (
+            ("leaf_search", f"leaf_search_{tag}", "dram_bytes_per_launch", "the launch of the full leaves"),
+            ("split_search", f"split_shared_{tag}", "dram_bytes_all_launches", "the two levels on shared nodes")):
+        rooflines[name]["traffic"] = traffic_from_profiles(summary, key=key)
+        rooflines[name]["ncu"] = counters_from_profiles(summary)
+        rooflines[name]["traffic_scope"] = scope
     return {"workload": f"{n} 64-bit keys (seed 2), l={leaf}, b={b}, {queries} member lookups",
             "value": n / (build_ms / 1e3), "unit": "keys/s", "build_ms": build_ms, "steps": steps,
             "lookup": {"value": queries / (statistics.median(lt) / 1e3), "unit": "queries/s"},
             "phases_ms": prof, "bits_per_key": stats["bits_per_key"],
             "work": {k: work[k] for k in ("split_nodes", "split_trials", "split_evals", "leaf_nodes", "leaf_trials",
                                           "leaf_evals", "split_evals_executed", "leaf_evals_executed")},
-            "rooflines": search_rooflines(prof, work, peak_ops), "tuning": tuning, "clocks": clocks}
+            "rooflines": rooflines, "tuning": tuning, "clocks": clocks}
 
 
 def batched_entry(rs, dev, stream, steps=2, warmup=1):
