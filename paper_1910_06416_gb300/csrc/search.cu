@@ -285,13 +285,15 @@ __device__ __forceinline__ int split_setup(const Node& nd, const uint64_t* table
   sp.unit = static_cast<uint32_t>(w1);
   sp.fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
   sp.bits = 32 - __clz(nd.m);
-  sp.magic = static_cast<uint32_t>((0x100000000ull + sp.unit - 1) / sp.unit);
+  // ceil(2^32 / unit), from the table (word 3): stored where the
+  // multiply-high gives floor(v / unit) for every v < m (always for m < 2^16
+  // and unit >= 2), else 0, and the search divides
+  sp.magic = static_cast<uint32_t>(table[kTableWords * nd.m + 3]);
   const uint32_t fields = sp.fanout - 1;
   sp.target = 0;
   for (uint32_t t = 0; t < fields; t++) sp.target |= uint64_t(sp.unit) << (t * sp.bits);
   sp.mask = fields * sp.bits >= 64 ? ~0ull : (1ull << (fields * sp.bits)) - 1;
-  // ceil(2^32 / unit) fits 32 bits only for unit >= 2; unit 1 (leaf size 1) divides
-  int mode = (nd.m >= 65536 || sp.unit < 2) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
+  int mode = (nd.m >= 65536 || sp.unit < 2 || sp.magic == 0) ? 2 : (fields * sp.bits <= 32 ? 0 : 1);
   if (sp.fanout == 4 && nd.m == 4 * sp.unit && nd.m < 256) {
     mode = 6;
     sp.cum_target = sp.unit | (sp.unit << 8) | (sp.unit << 16);
@@ -341,8 +343,8 @@ __device__ __forceinline__ void partition_node(const SearchArgs& a, const Node& 
   const uint64_t* table = a.table[cls];
   const uint64_t w1 = table[kTableWords * nd.m + 1];
   const uint32_t unit = static_cast<uint32_t>(w1), fanout = static_cast<uint32_t>(w1 >> 32) & 0xFF;
-  const bool divide = nd.m >= 65536 || unit < 2;
-  const uint32_t magic = divide ? 0u : static_cast<uint32_t>((0x100000000ull + unit - 1) / unit);
+  const uint32_t magic = static_cast<uint32_t>(table[kTableWords * nd.m + 3]);  // ceil(2^32 / unit) or 0
+  const bool divide = nd.m >= 65536 || unit < 2 || magic == 0;
   const uint64_t* src = a.keys[depth & 1] + nd.start;
   uint64_t* dst = a.keys[(depth + 1) & 1] + nd.start;
   if (tig == 0) {
@@ -773,6 +775,7 @@ __device__ __forceinline__ uint64_t leaf_round_two_phase(const uint64_t (&x)[L],
   const uint32_t below = (1u << lane) - 1;
   uint32_t nsurv = 0;
   uint64_t k = index_key(base + lane, dkey);
+#pragma unroll 4
   for (uint32_t j = 0; j < spl; j++, k += kLaneStep) {
     const uint64_t kp = k ^ (k >> 30);
     uint32_t seen = 0;
@@ -1101,20 +1104,21 @@ __global__ void __launch_bounds__(kThreads, leaf_min_blocks(LMAX)) k_leaves(Sear
           }
         }
       } else
-      for (uint64_t base = uint64_t(wig) * span;; base += uint64_t(gwarps) * span) {
+      // one compare per round: the stall point until it is checked, then the limit
+      for (uint64_t base = uint64_t(wig) * span, next_check = min(stall, limit);; base += uint64_t(gwarps) * span) {
         if (gwarps > 1 && __any_sync(0xFFFFFFFFu, base >= volatile_load(&best[gid]))) break;
         if ((++rounds & 255) == 0 &&
             __shfl_sync(0xFFFFFFFFu, lane == 0 ? *reinterpret_cast<volatile int*>(a.error) : 0, 0))
           break;  // another search failed, or the host cancelled the build
-        if (base >= limit) {
-          if (lane == 0) {
-            set_error(a.error, RECSPLIT_E_SEARCH_LIMIT);
-            atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), 0ull);
+        if (base >= next_check) {
+          if (base >= limit) {
+            if (lane == 0) {
+              set_error(a.error, RECSPLIT_E_SEARCH_LIMIT);
+              atomicMin(reinterpret_cast<unsigned long long*>(&best[gid]), 0ull);
+            }
+            break;
           }
-          break;
-        }
-        if (!checked && base >= stall) {
-          checked = true;
+          next_check = limit;
           bool dup = false;
 #pragma unroll
           for (int i = 0; i < LMAX; i++)
