@@ -309,14 +309,14 @@ int recsplit_server_stats(recsplit_server_t* srv, recsplit_server_stats_t* st);
  * and implicit synchronisation).  keys and out may be host or device memory;
  * results equal recsplit_lookup_u64's.  Keys and results are staged through
  * one fixed 16 MiB array in device memory that belongs to the library image
- * (every GPU that loads the library holds it until the process exits).  The
- * first call on a device looks up that array's device address, so make it
- * before any stream capture.  Every call on a device shares the array, so the
- * library runs them one at a time (a host lock held from the copy of the keys
- * until the results are in out): calls from several host threads are safe
- * and wait for each other.  q above the maximum fails with RECSPLIT_E_INVALID.
- * Every call, failed ones included, synchronizes `stream` before it returns
- * (the results are in out on success). */
+ * (every GPU that loads the library holds it until the process exits).
+ * Every call synchronizes `stream` (below), so none may be made while that
+ * stream is being captured into a CUDA graph.  Every call on a device shares
+ * the array, so the library runs them one at a time (a host lock held from
+ * the copy of the keys until the results are in out): calls from several
+ * host threads are safe and wait for each other.  q above the maximum fails
+ * with RECSPLIT_E_INVALID.  Every call, failed ones included, synchronizes
+ * `stream` before it returns (the results are in out on success). */
 int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64_t q, uint64_t* out, void* stream);
 
 /* Launch shapes of the seed searches for one leaf size.  They change only
@@ -326,9 +326,11 @@ int recsplit_lookup_u64_static(const recsplit_t* h, const uint64_t* keys, uint64
  *  leaf_seeds_per_lane: indices each lane tests per round (1, 2, 4 or 8)
  *  split_warps[k]: warps per split node for levels whose largest node has
  *                <64 (k=0), <256 (k=1) or more (k=2) keys (1, 2, 4 or 8)
- *  leaf_two_phase: 1 = test the first half of a leaf's keys for all of a
- *                round's indices first and finish only the survivors (pays
- *                for large leaves), 0 = test every index on all keys */
+ *  leaf_two_phase: 1 = phased test: map the first keys of a leaf for all of
+ *                a round's indices and finish only the survivors (two phases
+ *                up to 12 keys; from 13, three phases whose survivors wait in
+ *                per-warp queues across rounds), 0 = test every index on
+ *                all keys */
 typedef struct recsplit_tuning {
   uint32_t leaf_warps;
   uint32_t leaf_chunk;
