@@ -383,7 +383,8 @@ def run_reference(a):
 def add_executed(rooflines, work, leaf_ms, split_ms, peak_ops):
     """Beside the full-model fraction (every trial counted as l or m
     evaluations), the fraction over the evaluations the searches executed:
-    the two-phase leaf test skips the second part of most indices, and every
+    the phased leaf tests skip the later parts of most indices, the two-phase
+    block test of shared split nodes the last keys of most indices, and every
     round of 32 indices is evaluated whole (counted on the device in the
     work-counting build)."""
     for name, key, ops, ms in (("leaf_search", "leaf_evals_executed", OPS_PER_LEAF_EVAL, leaf_ms),

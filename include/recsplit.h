@@ -208,9 +208,11 @@ typedef struct recsplit_profile {
   uint32_t launches;      /* kernels launched by the build                      */
   uint32_t split_levels;  /* launches of the split search (one per tree level)  */
   uint64_t leaf_evals_executed;   /* hash evaluations the leaf searches executed: the
-                                     two-phase test skips the second part of most
+                                     phased tests skip the later parts of most
                                      indices, and every round is evaluated whole     */
-  uint64_t split_evals_executed;  /* the same for the split searches                 */
+  uint64_t split_evals_executed;  /* the same for the split searches (the two-phase
+                                     test of shared nodes skips the last keys of
+                                     most indices)                                   */
 } recsplit_profile_t;
 
 /* Per-build profiling for the calling host thread: 0 off; 1 phase events
