@@ -29,16 +29,11 @@ __device__ __forceinline__ uint64_t ef_offset(const View& v, uint64_t b, uint64_
   return static_cast<uint64_t>(z + static_cast<int64_t>(bs));
 }
 
-// Descent of a bucket of m >= 2 keys whose code starts at bit o: the minimal
-// structure's path (descend_min) and the path of the perfect, non-minimal
-// variant with its output ranges (descend_range).  RANGE: the structure has a
-// leaf range extra; false compiles the minimal structure's path alone.
-__device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
-__device__ __forceinline__ uint64_t descend_range(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
+// Descent of a bucket of m >= 2 keys whose code starts at bit o.  RANGE: the
+// structure has a leaf range extra (perfect, non-minimal variant); false
+// compiles the minimal structure's path alone.
 template <bool RANGE>
-__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
-  return RANGE ? descend_range(v, s0, m, o, lo) : descend_min(v, s0, m, o, lo);
-}
+__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo);
 
 // Output range of a subtree of m keys (table word 3, upper half).
 __device__ __forceinline__ uint64_t node_range(const View& v, uint64_t m) {
@@ -100,13 +95,7 @@ __device__ __forceinline__ uint64_t lookup_decoded(const View& v, const uint64_t
 // two bits per key and the build rejects one that reaches 2^32 bits, so
 // positions fit 32-bit registers.  32-bit words make every mask, shift, find
 // and count a single instruction.
-__device__ __forceinline__ uint32_t code_bits(const uint32_t* __restrict__ t, uint32_t pos, uint32_t width) {
-  const uint32_t w = pos >> 5, o = pos & 31;
-  const uint32_t lo = __ldg(t + w);
-  const uint32_t hi = o + width > 32 ? __ldg(t + w + 1) : 0u;
-  return __funnelshift_r(lo, hi, o) & ((1u << width) - 1);  // width <= 31
-}
-
+//
 // Scans stop at `end`, the 32-bit words from t to the end of the tree
 // section, and then return 2^32 - 1: the structure check of deserialize
 // already guarantees that every bucket's unary part holds its codes' one
@@ -170,7 +159,7 @@ __device__ __forceinline__ uint64_t window64(const uint32_t* __restrict__ t, uin
 constexpr uint64_t kWeyl64 = kWeyl << 6;
 
 // Sec. 4 / 6.2: descent of the splitting tree of a bucket of m >= 2 keys
-// whose code starts at bit o, for the minimal structure.  Per node of m keys
+// whose code starts at bit o.  Per node of m keys
 // one 16-byte lookup record gives r, the fanout, the part size, the
 // reciprocal for the part index, and the fixed bits and codes of a part-sized
 // subtree (to skip the earlier siblings).  The unary part of the bucket's
@@ -180,8 +169,12 @@ constexpr uint64_t kWeyl64 = kWeyl << 6;
 // window runs out (buckets of thousands of keys), a scan of the code words
 // finds the position and the window is reloaded there: the chosen subtree's
 // codes follow it, so the rest of the descent reads the new window.  Fixed parts
-// are read with two loads and a funnel shift, without a branch.
-__device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
+// are read with two loads and a funnel shift, without a branch.  With a leaf
+// range extra e (RANGE), a leaf of m keys maps into m + e values and the
+// siblings left behind contribute their output ranges (table word 3) instead
+// of their keys.
+template <bool RANGE>
+__device__ __forceinline__ uint64_t descend(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
   const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
   const uint64_t left = v.tree_words32 - (o >> 5);
   const uint32_t end = left < 0xFFFFFFFFull ? static_cast<uint32_t>(left) : 0xFFFFFFFFu;
@@ -218,8 +211,9 @@ __device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint
     const uint64_t seed = (uint64_t(one - up) << r) | low;
     up = one + 1;
     const uint64_t k = seed * kWeyl64 + dkey;
-    const uint32_t val = __umulhi(family_top32(xpre, k ^ (k >> 30)), m);
-    if (fanout == 0) return s0 + c + val;
+    const uint32_t h = family_top32(xpre, k ^ (k >> 30));
+    if (fanout == 0) return s0 + c + __umulhi(h, RANGE ? m + v.extra : m);
+    const uint32_t val = __umulhi(h, m);
     const uint32_t part = min(nd.y ? __umulhi(val, nd.y) : val / nd.x, fanout - 1);
     if (part) {
       fixed += part * nd.z;
@@ -240,61 +234,13 @@ __device__ __forceinline__ uint64_t descend_min(const View& v, uint64_t s0, uint
           win = window64(t, u0 + wb, end);
         }
       }
-      c += part * nd.x;
+      // keys (or, with a leaf range extra, output ranges) of the siblings left behind
+      c += RANGE ? static_cast<uint32_t>(part * node_range(v, nd.x)) : part * nd.x;
     }
     m = part + 1 < fanout ? nd.x : m - nd.x * (fanout - 1);
     if (m <= 1) return s0 + c;
     nd = __ldg(rec + m);
     dkey += kWeyl;
-  }
-}
-
-// The same descent for structures with a leaf range extra (perfect,
-// non-minimal variant): leaves map into m + e values, and the siblings left
-// behind contribute their output ranges.
-__device__ __forceinline__ uint64_t descend_range(const View& v, uint64_t s0, uint32_t m, uint64_t o, uint64_t lo) {
-  const uint32_t extra = v.extra;
-  const uint32_t* __restrict__ t = reinterpret_cast<const uint32_t*>(v.tree) + (o >> 5);
-  const uint64_t left = v.tree_words32 - (o >> 5);
-  const uint32_t end = left < 0xFFFFFFFFull ? static_cast<uint32_t>(left) : 0xFFFFFFFFu;
-  uint32_t fixed = static_cast<uint32_t>(o & 31);
-  uint32_t c = 0;
-  const uint64_t xpre = pre_key(lo);
-  // words 0 and 1 of the node-size table: subtree fixed bits | codes << 32;
-  // unit | fanout << 32 | r << 40
-  ulonglong2 tw = __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * m));
-  uint32_t unary = fixed + static_cast<uint32_t>(tw.x);
-  for (uint32_t depth = 0;; depth++) {
-    const uint32_t r = static_cast<uint32_t>(tw.y >> 40) & 31;
-    const uint32_t fanout = static_cast<uint32_t>(tw.y >> 32) & 0xFF;
-    const uint32_t unit = static_cast<uint32_t>(tw.y);
-    const uint32_t low = code_bits(t, fixed, r);
-    fixed += r;
-    const uint32_t one = code_next_one(t, unary, end);
-    if (one == ~0u) return ~0ull;
-    const uint64_t seed = (uint64_t(one - unary) << r) | low;
-    unary = one + 1;
-    if (fanout == 0) return s0 + c + phi_pre(xpre, family_key(seed, depth), m + extra);
-    const uint32_t val = phi_pre(xpre, family_key(seed, depth), m);
-    const uint32_t magic = static_cast<uint32_t>(__ldg(v.table + kTableWords * m + 3));
-    const uint32_t part = min(magic ? __umulhi(val, magic) : val / unit, fanout - 1);
-    const uint32_t next = part + 1 < fanout ? unit : m - unit * (fanout - 1);
-    const ulonglong2 tn = __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * next));
-    if (part) {
-      const ulonglong2 tu = part + 1 < fanout ? tn : __ldg(reinterpret_cast<const ulonglong2*>(v.table + kTableWords * unit));
-      fixed += part * static_cast<uint32_t>(tu.x);
-      const uint32_t skip = part * static_cast<uint32_t>(tu.x >> 32);
-      if (skip) {
-        const uint32_t at = code_select(t, unary, skip - 1, end);
-        if (at == ~0u) return ~0ull;
-        unary = at + 1;
-      }
-      // keys (or, with a leaf range extra, output ranges) of the siblings left behind
-      c += extra ? static_cast<uint32_t>(part * node_range(v, unit)) : part * unit;
-    }
-    m = next;
-    tw = tn;
-    if (m <= 1) return s0 + c;
   }
 }
 
