@@ -2,8 +2,9 @@
 
 The search kernel for full leaves is compiled once per leaf size (Sec. 5.2:
 the bijection test of l keys); each size here runs on key sets whose buckets
-produce full l-key leaves, with the two-phase test (the default from l = 10)
-and with the one-phase test, and the structures must equal the oracle's.
+produce full l-key leaves, with the phased test (the default from l = 10:
+two phases up to 12 keys, three phases with per-warp survivor queues from
+13) and with the one-phase test, and the structures must equal the oracle's.
 Sizes 22 to 24 take the oracle minutes per leaf and are checked against
 stored oracle digests (test_gpu_digests.py).
 """
